@@ -1,0 +1,180 @@
+/*
+ * psl1.h -- C ABI of the GB300 parareal / L1 / sine-Galerkin solver for the
+ * quasilinear Caputo subdiffusion equation (arXiv 2510.11023)
+ *
+ *     d^alpha_t u = div( D(x,t,u) grad u ) + f(x,t,u)   on a box Omega,
+ *     u = 0 on the boundary,  u(.,0) = u0,  0 < alpha <= 1        (Sec. 1, Eq. MainPDE)
+ *
+ * Space: Galerkin in the L2-orthonormal sine basis
+ *   1D  phi_k(x) = sqrt(2/L) sin(k pi (x-lo)/L),   k = 1..Mx
+ *   2D  phi_kl(x,y) = phi_k(x) phi_l(y),  mode index i = (k-1)*My + (l-1)
+ * with Gauss-Legendre quadrature (Qx [x Qy] nodes) for the D and f terms and
+ * the identity mass matrix (Sec. 2.1, Eq. AForm / MainPDEWeakSemi).
+ * Time: the semi-implicit L1 scheme (Sec. 2.1, Eq. L1Scheme and
+ * NumericalSchemeSequential): D and f are evaluated at the previous time
+ * level, so every step is one SPD solve (I + mu A(D)) c_new = history + mu F.
+ * Parallel in time: parareal with the coarse propagator G_n (one L1 step of
+ * size dT = T/P with the whole coarse history, Eq. CoarsePropagator) and the
+ * fine propagator F_n (m = N/P fine steps whose history on [0,T_n] is taken
+ * on the coarse grid, Sec. 2.2, Eq. L1Fine / NumericalSchemeFine /
+ * FinePropagator), iterated as in Eq. (Parareal) and Fig. (parareal).
+ *
+ * Everything runs on one CUDA device in hand-written sm_103a kernels; there
+ * is no CPU fallback: a call that needs the device fails with PSL1_ERR_CUDA
+ * when none is usable.
+ *
+ * Conventions
+ *  - Every function returns a psl1_status and never aborts the process; the
+ *    text of the last failure is returned by psl1_last_error(handle) (or
+ *    psl1_last_error(NULL) for a failed psl1_create).
+ *  - Ownership: the caller owns every array it passes; the library copies
+ *    what it keeps.  Host arrays are plain C arrays; "_dev" functions take
+ *    device pointers and are ordered on the handle's stream.
+ *  - A handle is not thread-safe; different handles are independent.
+ *  - Coefficient vectors of a batch are concatenated instance after instance
+ *    (instance b holds K_b = Mx*My doubles); "node" arrays hold the P+1
+ *    coarse nodes T_0..T_P of every instance: sum_b (P+1)*K_b doubles.
+ */
+#ifndef PSL1_H
+#define PSL1_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psl1_problem* psl1_h;
+
+typedef enum {
+    PSL1_OK = 0,
+    PSL1_ERR_ARG = -1,           /* invalid argument or size                       */
+    PSL1_ERR_NOT_SPD = -2,       /* non-positive Cholesky pivot (D <= 0 somewhere)  */
+    PSL1_ERR_NONFINITE = -3,     /* NaN / Inf produced or supplied                  */
+    PSL1_ERR_CUDA = -4,          /* CUDA runtime failure or no usable device        */
+    PSL1_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up              */
+    PSL1_ERR_NOT_CONVERGED = -6, /* parareal stopped at max_iter above tolerance    */
+    PSL1_ERR_STATE = -7,         /* call out of order (e.g. get before solve)       */
+    PSL1_ERR_NOMEM = -8          /* device or host allocation failed                */
+} psl1_status;
+
+/* Precision of the solve (the history sums, L1 weights and parareal
+ * correction are FP64 in every mode).
+ *  FP64 : plain FP64 everywhere (transforms, assembly, Cholesky).
+ *  MIXED: FP32-pair ("double-float") transforms and residuals, FP32 Cholesky
+ *         factor with iterative refinement against the FP64-accurate operator.
+ *  FP32 : FP32 transforms, assembly and Cholesky; no refinement.            */
+enum { PSL1_PREC_FP64 = 0, PSL1_PREC_MIXED = 1, PSL1_PREC_FP32 = 2 };
+
+/* Serial solvers.
+ *  HYBRID : U_{n+1} = F_n(U_{0:n}), n = 0..P-1 -- the sequential fine sweep,
+ *           the fixed point of parareal (Sec. 2.2, Eq. PararealConvergence).
+ *  UNIFORM: the uniform L1 scheme on all N fine steps with the whole fine
+ *           history (Sec. 2.1, Eq. NumericalSchemeSequential with dt = T/N).
+ *  COARSE : U_{n+1} = G_n(U_{0:n}) -- the coarse sweep (parareal step 1).   */
+enum { PSL1_SERIAL_HYBRID = 0, PSL1_SERIAL_UNIFORM = 1, PSL1_SERIAL_COARSE = 2 };
+
+/* One problem instance.  Coefficient families (x, y physical coordinates):
+ *   D = (d0 + d1/(1+u^2) * X1 + d2*u + d3*sin(pi x)) * X0,
+ *       X_i = 1 + a_i sin(2 pi x) + b_i cos(2 pi y)      (b_i terms 2D only)
+ *       dpar = {d0, d1, d2, d3, a0, b0, a1, b1}
+ *   f = c0 cos u + c1 sin u + c2 u (1-u) + c3 sin(pi x) e^{-t}
+ *       + c4 S1(x,t) + c5 S2(x,t),        fpar = {c0, c1, c2, c3, c4, c5, 0, 0}
+ * S1, S2 are the manufactured sources of the exact solutions
+ *   S1: u = (1 + t^alpha) sin(pi x)            with D = d0 + d1/(1+u^2)
+ *   S2: u = (1 + t^2) sin(pi x)/(2 - cos pi x)  with D = d0 + d3 sin(pi x)
+ * on (0,1) (1D only).                                                       */
+typedef struct {
+    int dim;          /* 1 or 2                                               */
+    int modes[2];     /* Mx, My (My unused in 1D); 1 <= Mx*My <= 4096         */
+    int qnodes[2];    /* Qx, Qy Gauss-Legendre nodes; 0 selects 2*modes; even */
+    int nsteps;       /* N: total fine L1 steps on [0,T]; a multiple of P     */
+    double alpha;     /* fractional order, 0 < alpha <= 1                      */
+    double T;         /* final time, > 0                                      */
+    double lo[2];     /* Omega = (lo0,hi0) [x (lo1,hi1)]                      */
+    double hi[2];
+    double dpar[8];
+    double fpar[8];
+} psl1_instance;
+
+/* Per-solve statistics filled by the library (device times by CUDA events). */
+typedef struct {
+    int    iterations_max;   /* largest parareal iteration count of the batch   */
+    int    kernel_launches;  /* launches of this library's kernels in the solve */
+    double ms_total;         /* wall time of the last solve call (host clock)   */
+    double ms_fine;          /* device time in fine-propagator launches         */
+    double ms_coarse;        /* device time in coarse sweeps                    */
+    double ms_history;       /* device time in history kernels                  */
+    double fine_steps;       /* linearised fine steps executed (all instances)  */
+    double fine_step_modes;  /* sum over executed fine steps of K               */
+} psl1_stats;
+
+/* Create a batch of `batch` instances sharing the slice count P (every
+ * instance's nsteps must be a multiple of P).  `cuda_stream` is a
+ * cudaStream_t to order all work on, or NULL for a library-owned stream.
+ * Builds the quadrature, trigonometric and L1 weight tables on the device.
+ * Errors: PSL1_ERR_ARG for an invalid description, PSL1_ERR_CUDA,
+ * PSL1_ERR_NOMEM.                                                          */
+psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* inst, int P,
+                        int precision, void* cuda_stream);
+
+/* Replace the D / f family parameters (batch x 8 doubles, host).            */
+psl1_status psl1_set_D(psl1_h h, const double* dpar);
+psl1_status psl1_set_f(psl1_h h, const double* fpar);
+
+/* Initial modal coefficients u0 (sum_b K_b doubles), host or device memory. */
+psl1_status psl1_set_u0(psl1_h h, const double* coeffs);
+psl1_status psl1_set_u0_dev(psl1_h h, const double* d_coeffs);
+
+/* Serial solve of every instance (kind: PSL1_SERIAL_*).  The result at the
+ * coarse nodes is kept in the "serial" slot (see psl1_get_coeffs).          */
+psl1_status psl1_solve_serial(psl1_h h, int kind);
+
+/* Parareal iteration (Eq. Parareal with the stored G_old of the flowchart):
+ * init U^0 by the coarse sweep, then iterate until
+ *   e_k = max_n ||U^{k+1}_n - U^k_n||_2 / max_n ||U^{k+1}_n||_2 <= tol
+ * for every instance, or k = max_iter (max_iter <= 0 selects P).  Slices
+ * n < k are already exact after k iterations and are not recomputed.
+ * iters_out (may be NULL) receives the largest iteration count.  Returns
+ * PSL1_ERR_NOT_CONVERGED (results still readable) if some instance stopped
+ * at max_iter above tol.                                                    */
+psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_out);
+
+/* Copy coefficients at the coarse nodes, sum_b (P+1) K_b doubles:
+ * which = 0: the current parareal iterate, 1: the last serial solve.       */
+psl1_status psl1_get_coeffs(psl1_h h, int which, double* out);
+psl1_status psl1_get_coeffs_dev(psl1_h h, int which, double* d_out);
+
+/* Per-instance parareal iteration counts (batch ints) and the increment log
+ * e_k of instance b (cap entries; len receives the count).                  */
+psl1_status psl1_get_iterations(psl1_h h, int* iters);
+psl1_status psl1_get_errlog(psl1_h h, int b, double* out, int cap, int* len);
+
+/* Iterate history: copy U^k (sum_b (P+1)K_b doubles) of parareal iteration k
+ * of the last psl1_solve_parareal (0 <= k <= iterations) -- available when the
+ * handle keeps iterates (psl1_keep_iterates(h, 1) before the solve).        */
+psl1_status psl1_keep_iterates(psl1_h h, int on);
+psl1_status psl1_get_iterate(psl1_h h, int k, double* out);
+
+/* Statistics of the last solve.                                             */
+psl1_status psl1_get_stats(psl1_h h, psl1_stats* st);
+
+/* ---- single pieces of the path, for checks at full size ----------------- */
+/* One linearised step of instance b (Eq. NumericalSchemeSequential form):
+ *   (I + mu A(D(t_e, c_prev))) c_new = hist + mu F(f(t_e, c_prev)),
+ * host arrays of K_b doubles.                                               */
+psl1_status psl1_step(psl1_h h, int b, const double* c_prev, double t_e, double mu,
+                      const double* hist, double* c_new);
+
+/* Fine propagator F_n of instance b on the coarse states U_0..U_n (host,
+ * (n+1) K_b doubles); V receives U_{n,0..m} ((m+1) K_b doubles).           */
+psl1_status psl1_fine_slice(psl1_h h, int b, int n, const double* U, double* V);
+
+/* Coarse propagator G_n of instance b on U_0..U_n (host); out: K_b doubles. */
+psl1_status psl1_coarse_step(psl1_h h, int b, int n, const double* U, double* out);
+
+const char* psl1_last_error(psl1_h h);
+void psl1_destroy(psl1_h h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSL1_H */

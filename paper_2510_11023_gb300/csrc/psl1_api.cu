@@ -1,0 +1,703 @@
+// psl1_api.cu -- C ABI (include/psl1.h): problem set-up, device pools, and
+// the host drivers of the serial solvers and of the parareal iteration.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/psl1.h"
+#include "psl1_kernels.h"
+
+using namespace psl1;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct psl1_problem {
+    int B = 0, P = 0, prec = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<psl1_instance> desc;
+    std::vector<InstDev> inst;
+    std::vector<TabDev> tabs;
+    std::string err;
+    int nsm = 0;
+    // sizes
+    long long sumK = 0, sumU = 0, sumPK = 0, sumB = 0, sumNK = 0, tabElems = 0;
+    int Kmax = 0, Kpmax = 0, Qhmax = 0, mmax = 0, Nmax = 0;
+    // device pools
+    std::vector<void*> allocs;
+    InstDev* d_inst = nullptr;
+    TabDev* d_tab = nullptr;
+    double *d_tp = nullptr, *d_bp = nullptr, *d_u0 = nullptr;
+    double *d_Ua = nullptr, *d_Ub = nullptr, *d_Us = nullptr, *d_Fv = nullptr, *d_Gold = nullptr;
+    double *d_incr = nullptr, *d_work = nullptr, *d_ring = nullptr;
+    int *d_nfirst = nullptr, *d_active = nullptr, *d_counter = nullptr;
+    int2* d_units = nullptr;
+    int nunits = 0;
+    DevStatus* d_status = nullptr;
+    // uniform solver pools (lazy)
+    double *d_Wcur = nullptr, *d_dW = nullptr, *d_part = nullptr;
+    int uni_chunk = 256, uni_maxchunks = 0;
+    PathArgs pa{};
+    // state
+    bool u0_set = false, par_done = false, ser_done = false;
+    double* d_Ucur = nullptr;   // buffer holding the current parareal iterate
+    std::vector<int> iters;
+    std::vector<std::vector<double>> errlog;
+    bool keep_iterates = false;
+    std::vector<std::vector<double>> iterates;
+    psl1_stats stats{};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+static psl1_status fail(psl1_problem* h, psl1_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+#define CU(h, call)                                                                                  \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail((h), PSL1_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                         \
+    } while (0)
+
+template <typename T>
+static psl1_status dalloc(psl1_problem* h, T** p, size_t count)
+{
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess)
+        return fail(h, PSL1_ERR_NOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return PSL1_OK;
+}
+
+#define TRY(x)                       \
+    do {                             \
+        psl1_status s_ = (x);        \
+        if (s_ != PSL1_OK) return s_; \
+    } while (0)
+
+static psl1_status check_device_status(psl1_problem* h)
+{
+    DevStatus st{};
+    CU(h, cudaMemcpyAsync(&st, h->d_status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    if (st.code != 0) {
+        const char* what = st.code == PSL1_ERR_NOT_SPD ? "non-positive Cholesky pivot (D <= 0?)"
+                           : st.code == PSL1_ERR_NONFINITE ? "non-finite value"
+                                                           : "device error";
+        return fail(h, (psl1_status)st.code, "%s in instance %d (stage %d, step %d)", what, st.inst, st.where,
+                    st.info);
+    }
+    return PSL1_OK;
+}
+
+static psl1_status reset_status(psl1_problem* h)
+{
+    CU(h, cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream));
+    return PSL1_OK;
+}
+
+static bool finite_all(const double* p, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+extern "C" {
+
+const char* psl1_last_error(psl1_h h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void psl1_destroy(psl1_h h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs) cudaFree(p);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+static psl1_status validate(const psl1_instance& d, int P, int b)
+{
+    if (d.dim != 1) return fail(nullptr, PSL1_ERR_ARG, "instance %d: dim must be 1 in this build", b);
+    int Mx = d.modes[0];
+    if (Mx < 1 || Mx > KMAX_1D) return fail(nullptr, PSL1_ERR_ARG, "instance %d: modes %d outside [1,%d]", b, Mx, KMAX_1D);
+    int Q = d.qnodes[0] ? d.qnodes[0] : 2 * Mx;
+    if (Q < 2 || (Q & 1) || Q > 4 * KMAX_1D)
+        return fail(nullptr, PSL1_ERR_ARG, "instance %d: quadrature nodes %d must be even in [2,%d]", b, Q, 4 * KMAX_1D);
+    if (d.nsteps < P || d.nsteps % P)
+        return fail(nullptr, PSL1_ERR_ARG, "instance %d: nsteps %d must be a positive multiple of P=%d", b, d.nsteps, P);
+    if (!(d.alpha > 0.0 && d.alpha <= 1.0)) return fail(nullptr, PSL1_ERR_ARG, "instance %d: alpha must be in (0,1]", b);
+    if (!(d.T > 0.0) || !std::isfinite(d.T)) return fail(nullptr, PSL1_ERR_ARG, "instance %d: T must be > 0", b);
+    if (!(d.hi[0] > d.lo[0]) || !std::isfinite(d.lo[0]) || !std::isfinite(d.hi[0]))
+        return fail(nullptr, PSL1_ERR_ARG, "instance %d: empty domain", b);
+    if (!finite_all(d.dpar, 8) || !finite_all(d.fpar, 8))
+        return fail(nullptr, PSL1_ERR_ARG, "instance %d: non-finite coefficient parameters", b);
+    return PSL1_OK;
+}
+
+psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, int precision, void* stream)
+{
+    if (!out) return fail(nullptr, PSL1_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (batch < 1 || !in) return fail(nullptr, PSL1_ERR_ARG, "batch must be >= 1 with an instance array");
+    if (P < 1) return fail(nullptr, PSL1_ERR_ARG, "P must be >= 1");
+    if (precision != PSL1_PREC_FP64)
+        return fail(nullptr, PSL1_ERR_ARG, "precision %d is not available in this build", precision);
+    for (int b = 0; b < batch; ++b) TRY(validate(in[b], P, b));
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1)
+        return fail(nullptr, PSL1_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+
+    psl1_problem* h = new psl1_problem();
+    h->B = batch;
+    h->P = P;
+    h->prec = precision;
+    h->desc.assign(in, in + batch);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return fail(nullptr, PSL1_ERR_CUDA, "stream creation failed");
+        }
+        h->own_stream = true;
+    }
+    auto bail = [&](psl1_status st) {
+        g_create_error = h->err;
+        psl1_destroy(h);
+        return st;
+    };
+#define CTRY(x)                                 \
+    do {                                        \
+        psl1_status s_ = (x);                   \
+        if (s_ != PSL1_OK) return bail(s_);     \
+    } while (0)
+
+    // tables shared by instances with the same (Mx, Qx, box)
+    std::map<std::tuple<int, int, double, double>, int> tabid;
+    std::vector<TableJob> jobs;
+    h->inst.resize(batch);
+    for (int b = 0; b < batch; ++b) {
+        const psl1_instance& d = in[b];
+        InstDev& I = h->inst[b];
+        memset(&I, 0, sizeof I);
+        I.dim = 1;
+        I.Mx = d.modes[0];
+        I.My = 1;
+        I.K = I.Mx;
+        I.nb = (I.K + TILE - 1) / TILE;
+        I.Kp = I.nb * TILE;
+        I.Q = d.qnodes[0] ? d.qnodes[0] : 2 * I.Mx;
+        I.Qh = I.Q / 2;
+        I.N = d.nsteps;
+        I.P = P;
+        I.m = I.N / P;
+        I.alpha = d.alpha;
+        I.T = d.T;
+        I.dT = d.T / P;
+        I.dt = d.T / I.N;
+        I.lo0 = d.lo[0];
+        I.hi0 = d.hi[0];
+        double L = I.hi0 - I.lo0;
+        I.cA = M_PI * M_PI / (L * L * L);
+        for (int i = 0; i < 8; ++i) {
+            I.dpar[i] = d.dpar[i];
+            I.fpar[i] = d.fpar[i];
+        }
+        auto key = std::make_tuple(I.Mx, I.Q, I.lo0, I.hi0);
+        auto it = tabid.find(key);
+        if (it == tabid.end()) {
+            TabDev t{};
+            t.Mx = I.Mx;
+            t.Qx = I.Q;
+            t.Qh = I.Qh;
+            long long o = h->tabElems;
+            t.oX = o;
+            o += t.Qh;
+            t.oWq = o;
+            o += t.Qh;
+            t.oAux = o;
+            o += 4LL * t.Qh;
+            t.oSt = o;
+            o += (long long)t.Mx * t.Qh;
+            t.oS = o;
+            o += (long long)t.Qh * t.Mx;
+            t.oC = o;
+            o += (long long)t.Qh * (2 * t.Mx + 1);
+            h->tabElems = o;
+            int id = (int)h->tabs.size();
+            h->tabs.push_back(t);
+            tabid[key] = id;
+            TableJob j{};
+            j.Mx = t.Mx;
+            j.Qh = t.Qh;
+            j.lo = I.lo0;
+            j.hi = I.hi0;
+            jobs.push_back(j);
+            I.tab = id;
+        } else {
+            I.tab = it->second;
+        }
+        I.Nb = std::max(std::max(I.N, P), I.m) + 1;
+        I.oK = h->sumK;
+        h->sumK += I.K;
+        I.oU = h->sumU;
+        h->sumU += (long long)(P + 1) * I.K;
+        I.oPK = h->sumPK;
+        h->sumPK += (long long)P * I.K;
+        I.oB = h->sumB;
+        h->sumB += (I.Nb + 1) + (long long)P * I.m;
+        I.oW = h->sumNK;
+        h->sumNK += (long long)I.N * I.K;
+        h->Kmax = std::max(h->Kmax, I.K);
+        h->Kpmax = std::max(h->Kpmax, I.Kp);
+        h->Qhmax = std::max(h->Qhmax, I.Qh);
+        h->mmax = std::max(h->mmax, I.m);
+        h->Nmax = std::max(h->Nmax, I.N);
+    }
+    int nbmax = h->Kpmax / TILE;
+    int nslots = std::max(2 * h->nsm, batch);
+    CTRY(dalloc(h, &h->d_inst, batch));
+    CTRY(dalloc(h, &h->d_tab, h->tabs.size()));
+    CTRY(dalloc(h, &h->d_tp, h->tabElems));
+    CTRY(dalloc(h, &h->d_bp, h->sumB));
+    CTRY(dalloc(h, &h->d_u0, h->sumK));
+    CTRY(dalloc(h, &h->d_Ua, h->sumU));
+    CTRY(dalloc(h, &h->d_Ub, h->sumU));
+    CTRY(dalloc(h, &h->d_Us, h->sumU));
+    CTRY(dalloc(h, &h->d_Fv, h->sumPK));
+    CTRY(dalloc(h, &h->d_Gold, h->sumPK));
+    CTRY(dalloc(h, &h->d_incr, batch));
+    CTRY(dalloc(h, &h->d_nfirst, batch));
+    CTRY(dalloc(h, &h->d_active, batch));
+    CTRY(dalloc(h, &h->d_counter, 1));
+    CTRY(dalloc(h, &h->d_status, 1));
+    long long work_stride = bp_elems(nbmax, TILE);
+    long long ring_stride = (long long)h->mmax * h->Kmax;
+    CTRY(dalloc(h, &h->d_work, (size_t)nslots * work_stride));
+    CTRY(dalloc(h, &h->d_ring, (size_t)nslots * ring_stride));
+    // fine units, longest first (cost ~ m K^3)
+    std::vector<int2> units;
+    for (int b = 0; b < batch; ++b)
+        for (int n = 0; n < P; ++n) units.push_back(make_int2(b, n));
+    std::stable_sort(units.begin(), units.end(), [&](int2 x, int2 y) {
+        const InstDev &a = h->inst[x.x], &c = h->inst[y.x];
+        double ca = (double)a.m * a.K * a.K * a.K, cc = (double)c.m * c.K * c.K * c.K;
+        return ca > cc;
+    });
+    h->nunits = (int)units.size();
+    CTRY(dalloc(h, &h->d_units, units.size()));
+    for (size_t t = 0; t < jobs.size(); ++t) {
+        const TabDev& T = h->tabs[t];
+        jobs[t].xh = h->d_tp + T.oX;
+        jobs[t].wh = h->d_tp + T.oWq;
+        jobs[t].aux = h->d_tp + T.oAux;
+        jobs[t].St = h->d_tp + T.oSt;
+        jobs[t].S = h->d_tp + T.oS;
+        jobs[t].C = h->d_tp + T.oC;
+    }
+    auto cu = [&](cudaError_t e2, const char* what) -> psl1_status {
+        if (e2 != cudaSuccess) return fail(h, PSL1_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e2));
+        return PSL1_OK;
+    };
+    CTRY(cu(cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(InstDev) * batch, cudaMemcpyHostToDevice, h->stream),
+            "copy instances"));
+    CTRY(cu(cudaMemcpyAsync(h->d_tab, h->tabs.data(), sizeof(TabDev) * h->tabs.size(), cudaMemcpyHostToDevice,
+                            h->stream), "copy tables"));
+    CTRY(cu(cudaMemcpyAsync(h->d_units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice,
+                            h->stream), "copy units"));
+    CTRY(cu(cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream), "status"));
+    for (auto& j : jobs) CTRY(cu(launch_tables(j, h->stream), "table kernels"));
+    CTRY(cu(launch_weights(h->d_inst, batch, h->d_bp, h->stream), "weight kernel"));
+    // constants computed on the device (mu, muT, ...) are needed on the host copy too
+    CTRY(cu(cudaMemcpyAsync(h->inst.data(), h->d_inst, sizeof(InstDev) * batch, cudaMemcpyDeviceToHost, h->stream),
+            "read constants"));
+    CTRY(cu(cudaStreamSynchronize(h->stream), "set-up"));
+    for (auto& ev : h->ev) CTRY(cu(cudaEventCreate(&ev), "events"));
+
+    PathArgs& a = h->pa;
+    a.inst = h->d_inst;
+    a.tab = h->d_tab;
+    a.tp = h->d_tp;
+    a.bp = h->d_bp;
+    a.status = h->d_status;
+    a.work = h->d_work;
+    a.work_stride = work_stride;
+    a.ring = h->d_ring;
+    a.ring_stride = ring_stride;
+    a.nslots = nslots;
+    a.Kmax = h->Kmax;
+    a.Kpmax = h->Kpmax;
+    a.Qhmax = h->Qhmax;
+    a.mmax = h->mmax;
+    a.prec = precision;
+    h->iters.assign(batch, 0);
+    h->errlog.assign(batch, {});
+    h->d_Ucur = h->d_Ua;
+    *out = h;
+    return PSL1_OK;
+#undef CTRY
+}
+
+psl1_status psl1_set_D(psl1_h h, const double* dpar)
+{
+    if (!h || !dpar) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    if (!finite_all(dpar, 8 * h->B)) return fail(h, PSL1_ERR_ARG, "non-finite D parameters");
+    for (int b = 0; b < h->B; ++b)
+        for (int i = 0; i < 8; ++i) h->inst[b].dpar[i] = h->desc[b].dpar[i] = dpar[8 * b + i];
+    CU(h, cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(InstDev) * h->B, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_set_f(psl1_h h, const double* fpar)
+{
+    if (!h || !fpar) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    if (!finite_all(fpar, 8 * h->B)) return fail(h, PSL1_ERR_ARG, "non-finite f parameters");
+    for (int b = 0; b < h->B; ++b)
+        for (int i = 0; i < 8; ++i) h->inst[b].fpar[i] = h->desc[b].fpar[i] = fpar[8 * b + i];
+    CU(h, cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(InstDev) * h->B, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_set_u0(psl1_h h, const double* c)
+{
+    if (!h || !c) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    if (!finite_all(c, (int)h->sumK)) return fail(h, PSL1_ERR_NONFINITE, "u0 holds a non-finite value");
+    CU(h, cudaMemcpyAsync(h->d_u0, c, sizeof(double) * h->sumK, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    h->u0_set = true;
+    return PSL1_OK;
+}
+
+psl1_status psl1_set_u0_dev(psl1_h h, const double* c)
+{
+    if (!h || !c) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    CU(h, cudaMemcpyAsync(h->d_u0, c, sizeof(double) * h->sumK, cudaMemcpyDeviceToDevice, h->stream));
+    h->u0_set = true;
+    return PSL1_OK;
+}
+
+static psl1_status ensure_uniform_pools(psl1_problem* h)
+{
+    if (h->d_dW) return PSL1_OK;
+    h->uni_maxchunks = (h->Nmax + h->uni_chunk - 1) / h->uni_chunk;
+    TRY(dalloc(h, &h->d_Wcur, h->sumK));
+    TRY(dalloc(h, &h->d_dW, h->sumNK));
+    TRY(dalloc(h, &h->d_part, (size_t)h->B * h->uni_maxchunks * h->Kmax));
+    return PSL1_OK;
+}
+
+static double elapsed(cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+static void count_work(psl1_problem* h, const std::vector<int>& nfirst, const std::vector<int>& active)
+{
+    for (int b = 0; b < h->B; ++b) {
+        if (!active[b]) continue;
+        const InstDev& I = h->inst[b];
+        double steps = (double)(h->P - nfirst[b]) * I.m;
+        h->stats.fine_steps += steps;
+        h->stats.fine_step_modes += steps * I.K;
+    }
+}
+
+psl1_status psl1_solve_serial(psl1_h h, int kind)
+{
+    if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
+    if (!h->u0_set) return fail(h, PSL1_ERR_STATE, "set u0 before solving");
+    auto t0 = std::chrono::steady_clock::now();
+    h->stats = psl1_stats{};
+    TRY(reset_status(h));
+    CU(h, cudaEventRecord(h->ev[0], h->stream));
+    if (kind == PSL1_SERIAL_HYBRID) {
+        CU(h, launch_serial_hyb(h->pa, h->B, h->d_u0, h->d_Us, h->stream));
+        h->stats.kernel_launches = 1;
+        for (int b = 0; b < h->B; ++b) {
+            h->stats.fine_steps += h->inst[b].N;
+            h->stats.fine_step_modes += (double)h->inst[b].N * h->inst[b].K;
+        }
+    } else if (kind == PSL1_SERIAL_COARSE) {
+        CU(h, launch_coarse_sweep(h->pa, h->B, h->d_u0, nullptr, h->d_Us, nullptr, h->d_Gold, 1, h->d_nfirst,
+                                  h->d_active, h->d_incr, h->stream));
+        h->stats.kernel_launches = 1;
+    } else if (kind == PSL1_SERIAL_UNIFORM) {
+        TRY(ensure_uniform_pools(h));
+        CU(h, launch_uni_init(h->pa, h->B, h->d_u0, h->d_Wcur, h->d_Us, h->stream));
+        int launches = 1;
+        for (int j = 0; j < h->Nmax; ++j) {
+            CU(h, launch_uni_hist(h->pa, h->B, h->d_dW, j, h->d_part, h->uni_chunk, h->uni_maxchunks, h->stream));
+            CU(h, launch_uni_step(h->pa, h->B, h->d_Wcur, h->d_dW, h->d_Us, j, h->d_part, h->uni_chunk,
+                                  h->uni_maxchunks, h->stream));
+            launches += (j > 0) ? 2 : 1;
+        }
+        h->stats.kernel_launches = launches;
+        for (int b = 0; b < h->B; ++b) {
+            h->stats.fine_steps += h->inst[b].N;
+            h->stats.fine_step_modes += (double)h->inst[b].N * h->inst[b].K;
+        }
+    } else {
+        return fail(h, PSL1_ERR_ARG, "unknown serial kind %d", kind);
+    }
+    CU(h, cudaEventRecord(h->ev[1], h->stream));
+    TRY(check_device_status(h));
+    h->stats.ms_fine = elapsed(h->ev[0], h->ev[1]);
+    h->stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    h->ser_done = true;
+    return PSL1_OK;
+}
+
+psl1_status psl1_keep_iterates(psl1_h h, int on)
+{
+    if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
+    h->keep_iterates = on != 0;
+    return PSL1_OK;
+}
+
+static psl1_status snapshot(psl1_problem* h, const double* d)
+{
+    std::vector<double> v((size_t)h->sumU);
+    CU(h, cudaMemcpyAsync(v.data(), d, sizeof(double) * h->sumU, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    h->iterates.push_back(std::move(v));
+    return PSL1_OK;
+}
+
+psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_out)
+{
+    if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
+    if (!h->u0_set) return fail(h, PSL1_ERR_STATE, "set u0 before solving");
+    if (!(tol >= 0.0)) return fail(h, PSL1_ERR_ARG, "tol must be >= 0");
+    auto t0 = std::chrono::steady_clock::now();
+    const int B = h->B, P = h->P;
+    int maxit = (max_iter <= 0 || max_iter > P) ? P : max_iter;
+    h->stats = psl1_stats{};
+    h->iterates.clear();
+    h->iters.assign(B, 0);
+    h->errlog.assign(B, {});
+    TRY(reset_status(h));
+    std::vector<int> nfirst(B, 0), active(B, 1);
+    std::vector<double> incr(B, 0.0);
+    double* Uk = h->d_Ua;
+    double* Uk1 = h->d_Ub;
+    CU(h, cudaMemcpyAsync(h->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, h->stream));
+    // step 1: U^0 by the coarse sweep, G_old(n) = G_n(U^0_{0:n})
+    CU(h, cudaEventRecord(h->ev[0], h->stream));
+    CU(h, launch_coarse_sweep(h->pa, B, h->d_u0, nullptr, Uk, nullptr, h->d_Gold, 1, h->d_nfirst, h->d_active,
+                              h->d_incr, h->stream));
+    CU(h, cudaEventRecord(h->ev[1], h->stream));
+    h->stats.kernel_launches = 1;
+    TRY(check_device_status(h));
+    h->stats.ms_coarse += elapsed(h->ev[0], h->ev[1]);
+    if (h->keep_iterates) TRY(snapshot(h, Uk));
+    int k = 0;
+    for (; k < maxit; ++k) {
+        for (int b = 0; b < B; ++b) nfirst[b] = k;
+        count_work(h, nfirst, active);
+        CU(h, cudaMemcpyAsync(h->d_nfirst, nfirst.data(), sizeof(int) * B, cudaMemcpyHostToDevice, h->stream));
+        CU(h, cudaMemcpyAsync(h->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, h->stream));
+        CU(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
+        CU(h, cudaEventRecord(h->ev[0], h->stream));
+        int grid = std::min(h->nunits, h->pa.nslots);
+        CU(h, launch_fstage(h->pa, Uk, h->d_Fv, h->d_units, h->nunits, h->d_counter, h->d_nfirst, h->d_active,
+                            grid, h->stream));
+        CU(h, cudaEventRecord(h->ev[1], h->stream));
+        CU(h, launch_coarse_sweep(h->pa, B, h->d_u0, Uk, Uk1, h->d_Fv, h->d_Gold, 0, h->d_nfirst, h->d_active,
+                                  h->d_incr, h->stream));
+        CU(h, cudaEventRecord(h->ev[2], h->stream));
+        h->stats.kernel_launches += 2;
+        CU(h, cudaMemcpyAsync(incr.data(), h->d_incr, sizeof(double) * B, cudaMemcpyDeviceToHost, h->stream));
+        TRY(check_device_status(h));
+        h->stats.ms_fine += elapsed(h->ev[0], h->ev[1]);
+        h->stats.ms_coarse += elapsed(h->ev[1], h->ev[2]);
+        std::swap(Uk, Uk1);
+        if (h->keep_iterates) TRY(snapshot(h, Uk));
+        int nact = 0;
+        for (int b = 0; b < B; ++b) {
+            if (!active[b]) continue;
+            h->errlog[b].push_back(incr[b]);
+            h->iters[b] = k + 1;
+            if (incr[b] <= tol)
+                active[b] = 0;
+            else
+                ++nact;
+        }
+        if (nact == 0) {
+            ++k;
+            break;
+        }
+    }
+    h->d_Ucur = Uk;
+    h->par_done = true;
+    int itmax = 0;
+    bool all_conv = true;
+    for (int b = 0; b < B; ++b) {
+        itmax = std::max(itmax, h->iters[b]);
+        bool conv = (!h->errlog[b].empty() && h->errlog[b].back() <= tol) || h->iters[b] >= P;
+        if (!conv) all_conv = false;
+    }
+    h->stats.iterations_max = itmax;
+    if (iters_out) *iters_out = itmax;
+    h->stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (!all_conv) return fail(h, PSL1_ERR_NOT_CONVERGED, "parareal stopped at max_iter=%d above tol", maxit);
+    return PSL1_OK;
+}
+
+psl1_status psl1_get_coeffs(psl1_h h, int which, double* out)
+{
+    if (!h || !out) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    const double* src = which == 0 ? h->d_Ucur : h->d_Us;
+    if ((which == 0 && !h->par_done) || (which == 1 && !h->ser_done) || (which != 0 && which != 1))
+        return fail(h, PSL1_ERR_STATE, "no result of that kind yet");
+    CU(h, cudaMemcpyAsync(out, src, sizeof(double) * h->sumU, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_get_coeffs_dev(psl1_h h, int which, double* out)
+{
+    if (!h || !out) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    const double* src = which == 0 ? h->d_Ucur : h->d_Us;
+    if ((which == 0 && !h->par_done) || (which == 1 && !h->ser_done) || (which != 0 && which != 1))
+        return fail(h, PSL1_ERR_STATE, "no result of that kind yet");
+    CU(h, cudaMemcpyAsync(out, src, sizeof(double) * h->sumU, cudaMemcpyDeviceToDevice, h->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_get_iterations(psl1_h h, int* it)
+{
+    if (!h || !it) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    for (int b = 0; b < h->B; ++b) it[b] = h->iters[b];
+    return PSL1_OK;
+}
+
+psl1_status psl1_get_errlog(psl1_h h, int b, double* out, int cap, int* len)
+{
+    if (!h || b < 0 || b >= h->B) return fail(h, PSL1_ERR_ARG, "bad instance index");
+    int n = (int)h->errlog[b].size();
+    if (len) *len = n;
+    if (out)
+        for (int i = 0; i < n && i < cap; ++i) out[i] = h->errlog[b][i];
+    return PSL1_OK;
+}
+
+psl1_status psl1_get_iterate(psl1_h h, int k, double* out)
+{
+    if (!h || !out) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    if (k < 0 || k >= (int)h->iterates.size())
+        return fail(h, PSL1_ERR_STATE, "iterate %d not kept (enable psl1_keep_iterates before solving)", k);
+    memcpy(out, h->iterates[k].data(), sizeof(double) * h->sumU);
+    return PSL1_OK;
+}
+
+psl1_status psl1_get_stats(psl1_h h, psl1_stats* st)
+{
+    if (!h || !st) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    *st = h->stats;
+    return PSL1_OK;
+}
+
+// ---------------------------------------------------------------- single pieces
+struct TmpDev {
+    psl1_problem* h;
+    std::vector<void*> p;
+    ~TmpDev()
+    {
+        for (void* q : p) cudaFree(q);
+    }
+    double* get(size_t n)
+    {
+        void* q = nullptr;
+        if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(double)) != cudaSuccess) return nullptr;
+        p.push_back(q);
+        return (double*)q;
+    }
+};
+
+psl1_status psl1_step(psl1_h h, int b, const double* c, double te, double mu, const double* hist, double* out)
+{
+    if (!h || !c || !hist || !out || b < 0 || b >= h->B) return fail(h, PSL1_ERR_ARG, "bad argument");
+    int K = h->inst[b].K;
+    TmpDev t{h};
+    double *dc = t.get(K), *dh = t.get(K), *dout = t.get(K);
+    if (!dc || !dh || !dout) return fail(h, PSL1_ERR_NOMEM, "scratch allocation failed");
+    TRY(reset_status(h));
+    CU(h, cudaMemcpyAsync(dc, c, sizeof(double) * K, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(dh, hist, sizeof(double) * K, cudaMemcpyHostToDevice, h->stream));
+    CU(h, launch_one_step(h->pa, b, dc, dh, te, mu, dout, h->stream));
+    CU(h, cudaMemcpyAsync(out, dout, sizeof(double) * K, cudaMemcpyDeviceToHost, h->stream));
+    return check_device_status(h);
+}
+
+psl1_status psl1_fine_slice(psl1_h h, int b, int n, const double* U, double* V)
+{
+    if (!h || !U || !V || b < 0 || b >= h->B || n < 0 || n >= h->P) return fail(h, PSL1_ERR_ARG, "bad argument");
+    const InstDev& I = h->inst[b];
+    TmpDev t{h};
+    double *dU = t.get((size_t)(n + 1) * I.K), *dV = t.get((size_t)(I.m + 1) * I.K);
+    if (!dU || !dV) return fail(h, PSL1_ERR_NOMEM, "scratch allocation failed");
+    TRY(reset_status(h));
+    CU(h, cudaMemcpyAsync(dU, U, sizeof(double) * (n + 1) * I.K, cudaMemcpyHostToDevice, h->stream));
+    CU(h, launch_one_slice(h->pa, b, n, dU, dV, h->stream));
+    CU(h, cudaMemcpyAsync(V, dV, sizeof(double) * (I.m + 1) * I.K, cudaMemcpyDeviceToHost, h->stream));
+    return check_device_status(h);
+}
+
+psl1_status psl1_coarse_step(psl1_h h, int b, int n, const double* U, double* out)
+{
+    if (!h || !U || !out || b < 0 || b >= h->B || n < 0 || n >= h->P) return fail(h, PSL1_ERR_ARG, "bad argument");
+    const InstDev& I = h->inst[b];
+    TmpDev t{h};
+    double *dU = t.get((size_t)(n + 1) * I.K), *dout = t.get(I.K);
+    if (!dU || !dout) return fail(h, PSL1_ERR_NOMEM, "scratch allocation failed");
+    TRY(reset_status(h));
+    CU(h, cudaMemcpyAsync(dU, U, sizeof(double) * (n + 1) * I.K, cudaMemcpyHostToDevice, h->stream));
+    CU(h, launch_one_coarse(h->pa, b, n, dU, dout, h->stream));
+    CU(h, cudaMemcpyAsync(out, dout, sizeof(double) * I.K, cudaMemcpyDeviceToHost, h->stream));
+    return check_device_status(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,425 @@
+// psl1_kernels.cu -- the parareal / serial solver kernels of the 1D path.
+//
+//   k_fstage        F stage: every active (instance, slice) unit runs its m
+//                   fine steps (Eq. NumericalSchemeFine); persistent CTAs pull
+//                   units from an atomic counter (units pre-sorted by cost).
+//   k_coarse_sweep  sequential coarse sweep with the parareal correction
+//                   U^{k+1}_{n+1} = G_n(U^{k+1}_{0:n}) + (F_old(n) - G_old(n))
+//                   (Eq. Parareal, G_old stored as in Fig. parareal), and the
+//                   increment e_k of the stopping test.
+//   k_serial_hyb    S_hyb: the sequential sweep U_{n+1} = F_n(U_{0:n}).
+//   k_uni_hist/step S_uni: full-history uniform L1 -- an HBM-streaming history
+//                   kernel over all instances plus one step CTA per instance.
+#include "psl1_kernels.h"
+#include "psl1_step.cuh"
+
+namespace psl1 {
+
+struct Carve {
+    double *cur, *hist, *nxt, *F;
+    StepSmem s;
+};
+
+__device__ __forceinline__ Carve carve(const PathArgs& a, char* base)
+{
+    double* p = reinterpret_cast<double*>(base);
+    Carve c;
+    c.cur = p;
+    p += a.Kmax;
+    c.hist = p;
+    p += a.Kmax;
+    c.nxt = p;
+    p += a.Kmax;
+    c.F = p;
+    p += a.Kmax;
+    c.s.v = p;
+    p += a.Kpmax;
+    c.s.wp = p;
+    p += a.Qhmax;
+    c.s.wm = p;
+    p += a.Qhmax;
+    c.s.fp = p;
+    p += a.Qhmax;
+    c.s.fm = p;
+    p += a.Qhmax;
+    c.s.g = p;
+    p += 2 * a.Kmax + 1;
+    c.s.bad = reinterpret_cast<int*>(p);
+    return c;
+}
+
+size_t step_smem_bytes(const PathArgs& a)
+{
+    return sizeof(double) * (size_t)(4 * a.Kmax + a.Kpmax + 4 * a.Qhmax + 2 * a.Kmax + 1) + 16;
+}
+
+enum { WHERE_FINE = 1, WHERE_COARSE = 2, WHERE_UNI = 3, WHERE_ONE = 4 };
+
+__device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, const double* c,
+                                       const double* hist, double te, double mu, double* out, Carve& cv)
+{
+    const TabDev& Tb = a.tab[I.tab];
+    BPack<double, TILE> A{a.work + (size_t)blockIdx.x * a.work_stride};
+    return step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
+}
+
+__device__ __forceinline__ void check_finite(const PathArgs& a, const double* v, int K, int ii, int where,
+                                             int info)
+{
+    for (int k = threadIdx.x; k < K; k += NT)
+        if (!isfinite(v[k])) report(a.status, -3, ii, where, info);
+}
+
+// F_n of instance ii on coarse states U (rows 0..n, global): m fine steps with
+// the local fine history kept in the CTA's ring and the coarse history
+// m^-a sum_{i=1}^n b(n-i+r/m) (U_i - U_{i-1})  (Eq. L1Fine, difference form).
+__device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, double* Vout, double* out,
+                           Carve& cv, double* ring)
+{
+    const InstDev& I = a.inst[ii];
+    const int K = I.K, m = I.m, tid = threadIdx.x;
+    const double* bF = a.bp + I.oB;
+    const double* bC = bF + I.Nb + 1;
+    for (int k = tid; k < K; k += NT) {
+        cv.cur[k] = U[(size_t)n * K + k];
+        if (Vout) Vout[k] = cv.cur[k];
+    }
+    __syncthreads();
+    for (int r = 1; r <= m; ++r) {
+        for (int k = tid; k < K; k += NT) {
+            double h = cv.cur[k];
+            for (int j = 1; j <= r - 1; ++j) h -= bF[r - j] * ring[(size_t)(j - 1) * K + k];
+            const double* bc = bC + (r - 1);
+            for (int i = 1; i <= n; ++i)
+                h -= bc[(size_t)(n - i) * m] * (U[(size_t)i * K + k] - U[(size_t)(i - 1) * K + k]);
+            cv.hist[k] = h;
+        }
+        __syncthreads();
+        int bad = do_step(a, I, cv.cur, cv.hist, I.dT * n + I.dt * (r - 1), I.mu, cv.nxt, cv);
+        if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_FINE, n * m + r);
+        check_finite(a, cv.nxt, K, ii, WHERE_FINE, n * m + r);
+        for (int k = tid; k < K; k += NT) {
+            ring[(size_t)(r - 1) * K + k] = cv.nxt[k] - cv.cur[k];
+            cv.cur[k] = cv.nxt[k];
+            if (Vout) Vout[(size_t)r * K + k] = cv.nxt[k];
+        }
+        __syncthreads();
+    }
+    for (int k = tid; k < K; k += NT) out[k] = cv.cur[k];
+    __syncthreads();
+}
+
+// G_n of instance ii on U (rows 0..n, global) -> cv.nxt.  History in the
+// difference form U_n - sum_{j=0}^{n-1} b_{n-j} (U_{j+1} - U_j) of Eq. L1Scheme.
+__device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, Carve& cv)
+{
+    const InstDev& I = a.inst[ii];
+    const int K = I.K, tid = threadIdx.x;
+    const double* bF = a.bp + I.oB;
+    for (int k = tid; k < K; k += NT) {
+        double c = U[(size_t)n * K + k], h = c;
+        for (int j = 0; j < n; ++j) h -= bF[n - j] * (U[(size_t)(j + 1) * K + k] - U[(size_t)j * K + k]);
+        cv.cur[k] = c;
+        cv.hist[k] = h;
+    }
+    __syncthreads();
+    int bad = do_step(a, I, cv.cur, cv.hist, I.dT * n, I.muT, cv.nxt, cv);
+    if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_COARSE, n);
+    check_finite(a, cv.nxt, K, ii, WHERE_COARSE, n);
+}
+
+__global__ void __launch_bounds__(NT) k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units,
+                                               int nunits, int* counter, const int* nfirst, const int* active)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve(a, smem_raw);
+    __shared__ int s_u;
+    double* ring = a.ring + (size_t)blockIdx.x * a.ring_stride;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_u = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_u;
+        if (u >= nunits) break;
+        const int ii = units[u].x, n = units[u].y;
+        if (!active[ii] || n < nfirst[ii]) continue;
+        const InstDev& I = a.inst[ii];
+        fine_slice(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_coarse_sweep(PathArgs a, const double* u0, const double* Uold,
+                                                     double* Unew, const double* Fv, double* Gold, int init,
+                                                     const int* nfirst, const int* active, double* incr)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve(a, smem_raw);
+    __shared__ double red[NT / 32];
+    __shared__ double s_num, s_den;
+    const int ii = blockIdx.x, tid = threadIdx.x;
+    const InstDev& I = a.inst[ii];
+    const int K = I.K, P = I.P;
+    double* U = Unew + I.oU;
+    if (!init && !active[ii]) {   // converged: carry the iterate into the other buffer
+        for (int e = tid; e < (P + 1) * K; e += NT) U[e] = Uold[I.oU + e];
+        return;
+    }
+    int n0 = 0;
+    if (init) {
+        for (int k = tid; k < K; k += NT) U[k] = u0[I.oK + k];
+    } else {
+        n0 = nfirst[ii];
+        for (int e = tid; e < (n0 + 1) * K; e += NT) U[e] = Uold[I.oU + e];
+    }
+    __syncthreads();
+    double* Go = Gold + I.oPK;
+    const double* Fo = Fv + I.oPK;
+    for (int n = n0; n < P; ++n) {
+        coarse_step(a, ii, n, U, cv);
+        for (int k = tid; k < K; k += NT) {
+            double g = cv.nxt[k];
+            size_t e = (size_t)n * K + k;
+            U[(size_t)(n + 1) * K + k] = init ? g : g + (Fo[e] - Go[e]);
+            Go[e] = g;
+        }
+        __syncthreads();
+    }
+    if (init) return;
+    // e_k = max_n ||U^{k+1}_n - U^k_n|| / max_n ||U^{k+1}_n||
+    if (tid == 0) {
+        s_num = 0.0;
+        s_den = 0.0;
+    }
+    const double* Uo = Uold + I.oU;
+    for (int n = 0; n <= P; ++n) {
+        double sd = 0.0, sn = 0.0;
+        for (int k = tid; k < K; k += NT) {
+            double x = U[(size_t)n * K + k], d = x - Uo[(size_t)n * K + k];
+            sd += d * d;
+            sn += x * x;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sd += __shfl_xor_sync(0xffffffffu, sd, o);
+            sn += __shfl_xor_sync(0xffffffffu, sn, o);
+        }
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = sd;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NT / 32; ++w) t += red[w];
+            s_num = fmax(s_num, sqrt(t));
+        }
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = sn;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NT / 32; ++w) t += red[w];
+            s_den = fmax(s_den, sqrt(t));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) incr[ii] = s_den > 0.0 ? s_num / s_den : s_num;
+}
+
+__global__ void __launch_bounds__(NT) k_serial_hyb(PathArgs a, const double* u0, double* Us)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve(a, smem_raw);
+    const int ii = blockIdx.x;
+    const InstDev& I = a.inst[ii];
+    double* U = Us + I.oU;
+    double* ring = a.ring + (size_t)blockIdx.x * a.ring_stride;
+    for (int k = threadIdx.x; k < I.K; k += NT) U[k] = u0[I.oK + k];
+    __syncthreads();
+    for (int n = 0; n < I.P; ++n) fine_slice(a, ii, n, U, nullptr, U + (size_t)(n + 1) * I.K, cv, ring);
+}
+
+__global__ void k_uni_init(const InstDev* inst, const double* u0, double* Wcur, double* Us)
+{
+    const InstDev& I = inst[blockIdx.x];
+    for (int k = threadIdx.x; k < I.K; k += blockDim.x) {
+        Wcur[I.oK + k] = u0[I.oK + k];
+        Us[I.oU + k] = u0[I.oK + k];
+    }
+}
+
+// Partial history sums of the uniform scheme at step j (computing W_{j+1}):
+//   part[c][k] = sum_{l in chunk c} b_{j-l} dW_l[k],  dW_l = W_{l+1} - W_l.
+// Reads each history row once per step; coalesced along modes.
+__global__ void __launch_bounds__(NT) k_uni_hist(const InstDev* inst, const double* bp, const double* dW, int j,
+                                                 double* part, int chunk, int maxchunks, int Kmax)
+{
+    const int ii = blockIdx.y, c = blockIdx.x;
+    const InstDev& I = inst[ii];
+    if (j >= I.N) return;
+    const int l0 = c * chunk;
+    if (l0 >= j) return;
+    const int l1 = min(j, l0 + chunk);
+    const double* bF = bp + I.oB;
+    const double* h = dW + I.oW;
+    double* out = part + ((size_t)ii * maxchunks + c) * Kmax;
+    for (int k = threadIdx.x; k < I.K; k += NT) {
+        double acc = 0.0;
+        for (int l = l0; l < l1; ++l) acc = fma(bF[j - l], h[(size_t)l * I.K + k], acc);
+        out[k] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_uni_step(PathArgs a, double* Wcur, double* dW, double* Us, int j,
+                                                 const double* part, int chunk, int maxchunks)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve(a, smem_raw);
+    const int ii = blockIdx.x, tid = threadIdx.x;
+    const InstDev& I = a.inst[ii];
+    if (j >= I.N) return;
+    const int K = I.K;
+    const int nch = (j + chunk - 1) / chunk;
+    for (int k = tid; k < K; k += NT) {
+        double c = Wcur[I.oK + k], h = c;
+        for (int q = 0; q < nch; ++q) h -= part[((size_t)ii * maxchunks + q) * a.Kmax + k];
+        cv.cur[k] = c;
+        cv.hist[k] = h;
+    }
+    __syncthreads();
+    int bad = do_step(a, I, cv.cur, cv.hist, I.dt * j, I.mu, cv.nxt, cv);
+    if (bad >= 0 && tid == 0) report(a.status, -2, ii, WHERE_UNI, j);
+    check_finite(a, cv.nxt, K, ii, WHERE_UNI, j);
+    const bool node = ((j + 1) % I.m) == 0;
+    for (int k = tid; k < K; k += NT) {
+        double x = cv.nxt[k];
+        dW[I.oW + (size_t)j * K + k] = x - cv.cur[k];
+        Wcur[I.oK + k] = x;
+        if (node) Us[I.oU + (size_t)((j + 1) / I.m) * K + k] = x;
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_one_step(PathArgs a, int ii, const double* c, const double* hist,
+                                                 double te, double mu, double* out)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve(a, smem_raw);
+    const InstDev& I = a.inst[ii];
+    for (int k = threadIdx.x; k < I.K; k += NT) {
+        cv.cur[k] = c[k];
+        cv.hist[k] = hist[k];
+    }
+    __syncthreads();
+    int bad = do_step(a, I, cv.cur, cv.hist, te, mu, cv.nxt, cv);
+    if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_ONE, bad);
+    check_finite(a, cv.nxt, I.K, ii, WHERE_ONE, 0);
+    for (int k = threadIdx.x; k < I.K; k += NT) out[k] = cv.nxt[k];
+}
+
+__global__ void __launch_bounds__(NT) k_one_slice(PathArgs a, int ii, int n, const double* U, double* V)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve(a, smem_raw);
+    const InstDev& I = a.inst[ii];
+    fine_slice(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring);
+}
+
+__global__ void __launch_bounds__(NT) k_one_coarse(PathArgs a, int ii, int n, const double* U, double* out)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve(a, smem_raw);
+    const InstDev& I = a.inst[ii];
+    coarse_step(a, ii, n, U, cv);
+    for (int k = threadIdx.x; k < I.K; k += NT) out[k] = cv.nxt[k];
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename Kern>
+static cudaError_t prep(Kern k, size_t smem)
+{
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_fstage(const PathArgs& a, const double* Uold, double* Fv, const int2* units, int nunits,
+                          int* counter, const int* nfirst, const int* active, int grid, cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    cudaError_t e = prep(k_fstage, sm);
+    if (e != cudaSuccess) return e;
+    if (grid > a.nslots) grid = a.nslots;
+    k_fstage<<<grid, NT, sm, s>>>(a, Uold, Fv, units, nunits, counter, nfirst, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, const double* Uold, double* Unew,
+                                const double* Fv, double* Gold, int init, const int* nfirst,
+                                const int* active, double* incr, cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    cudaError_t e = prep(k_coarse_sweep, sm);
+    if (e != cudaSuccess) return e;
+    k_coarse_sweep<<<B, NT, sm, s>>>(a, u0, Uold, Unew, Fv, Gold, init, nfirst, active, incr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_serial_hyb(const PathArgs& a, int B, const double* u0, double* Us, cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    cudaError_t e = prep(k_serial_hyb, sm);
+    if (e != cudaSuccess) return e;
+    k_serial_hyb<<<B, NT, sm, s>>>(a, u0, Us);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uni_init(const PathArgs& a, int B, const double* u0, double* Wcur, double* Us, cudaStream_t s)
+{
+    k_uni_init<<<B, 256, 0, s>>>(a.inst, u0, Wcur, Us);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uni_hist(const PathArgs& a, int B, const double* dW, int j, double* part, int chunk,
+                            int maxchunks, cudaStream_t s)
+{
+    int nch = (j + chunk - 1) / chunk;
+    if (nch <= 0) return cudaSuccess;
+    dim3 grid(nch, B);
+    k_uni_hist<<<grid, NT, 0, s>>>(a.inst, a.bp, dW, j, part, chunk, maxchunks, a.Kmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uni_step(const PathArgs& a, int B, double* Wcur, double* dW, double* Us, int j,
+                            const double* part, int chunk, int maxchunks, cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    cudaError_t e = prep(k_uni_step, sm);
+    if (e != cudaSuccess) return e;
+    k_uni_step<<<B, NT, sm, s>>>(a, Wcur, dW, Us, j, part, chunk, maxchunks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_one_step(const PathArgs& a, int b, const double* c, const double* hist, double te, double mu,
+                            double* out, cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    cudaError_t e = prep(k_one_step, sm);
+    if (e != cudaSuccess) return e;
+    k_one_step<<<1, NT, sm, s>>>(a, b, c, hist, te, mu, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_one_slice(const PathArgs& a, int b, int n, const double* U, double* V, cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    cudaError_t e = prep(k_one_slice, sm);
+    if (e != cudaSuccess) return e;
+    k_one_slice<<<1, NT, sm, s>>>(a, b, n, U, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_one_coarse(const PathArgs& a, int b, int n, const double* U, double* out, cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    cudaError_t e = prep(k_one_coarse, sm);
+    if (e != cudaSuccess) return e;
+    k_one_coarse<<<1, NT, sm, s>>>(a, b, n, U, out);
+    return cudaGetLastError();
+}
+
+}  // namespace psl1

@@ -1,0 +1,56 @@
+// psl1_kernels.h -- host-side launch interface of the solver kernels
+// (internal to the library; the public boundary is include/psl1.h).
+#pragma once
+#include <cuda_runtime.h>
+#include "psl1_device.cuh"
+
+namespace psl1 {
+
+struct TableJob {
+    int Mx, Qh;
+    double lo, hi;
+    double *xh, *wh, *St, *S, *C, *aux;
+};
+
+// Pointers and sizes every solver kernel needs.
+struct PathArgs {
+    const InstDev* inst;
+    const TabDev* tab;
+    const double* tp;        // table pool
+    const double* bp;        // L1 weight pool
+    DevStatus* status;
+    double* work;            // per-CTA-slot matrix workspace (FP64 factor)
+    long long work_stride;   // doubles per slot
+    double* ring;            // per-CTA-slot fine history ring (m x K doubles)
+    long long ring_stride;
+    int nslots;              // slots available in work/ring
+    int Kmax, Kpmax, Qhmax, mmax;
+    int prec;                // PSL1_PREC_*
+};
+
+size_t step_smem_bytes(const PathArgs& a);
+
+cudaError_t launch_tables(const TableJob& job, cudaStream_t s);
+cudaError_t launch_weights(InstDev* inst, int B, double* bpool, cudaStream_t s);
+
+// Parareal pieces.
+cudaError_t launch_fstage(const PathArgs& a, const double* Uold, double* Fv, const int2* units, int nunits,
+                          int* counter, const int* nfirst, const int* active, int grid, cudaStream_t s);
+cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, const double* Uold, double* Unew,
+                                const double* Fv, double* Gold, int init, const int* nfirst,
+                                const int* active, double* incr, cudaStream_t s);
+// Serial solvers.
+cudaError_t launch_serial_hyb(const PathArgs& a, int B, const double* u0, double* Us, cudaStream_t s);
+cudaError_t launch_uni_init(const PathArgs& a, int B, const double* u0, double* Wcur, double* Us,
+                            cudaStream_t s);
+cudaError_t launch_uni_hist(const PathArgs& a, int B, const double* dW, int j, double* part, int chunk,
+                            int maxchunks, cudaStream_t s);
+cudaError_t launch_uni_step(const PathArgs& a, int B, double* Wcur, double* dW, double* Us, int j,
+                            const double* part, int chunk, int maxchunks, cudaStream_t s);
+// Single pieces (one CTA).
+cudaError_t launch_one_step(const PathArgs& a, int b, const double* c, const double* hist, double te,
+                            double mu, double* out, cudaStream_t s);
+cudaError_t launch_one_slice(const PathArgs& a, int b, int n, const double* U, double* V, cudaStream_t s);
+cudaError_t launch_one_coarse(const PathArgs& a, int b, int n, const double* U, double* out, cudaStream_t s);
+
+}  // namespace psl1

@@ -1,0 +1,262 @@
+"""Thin ctypes binding of the C ABI in ``include/psl1.h``.
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``libpsl1.so``.  There is no fallback; if the library cannot be built or
+loaded, or no CUDA device is usable, the calls raise ``PSL1Error``.
+
+Module-level functions carry the C names (``psl1_create``, ...); ``Problem``
+is a small convenience wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+from .workloads import InstanceSpec, Workload
+
+PREC = {"fp64": 0, "mixed": 1, "fp32": 2}
+SERIAL = {"hybrid": 0, "uniform": 1, "coarse": 2}
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOT_SPD", -3: "ERR_NONFINITE", -4: "ERR_CUDA", -5: "ERR_TIMEOUT",
+          -6: "ERR_NOT_CONVERGED", -7: "ERR_STATE", -8: "ERR_NOMEM"}
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+class PSL1Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("modes", ctypes.c_int * 2), ("qnodes", ctypes.c_int * 2),
+                ("nsteps", ctypes.c_int), ("alpha", ctypes.c_double), ("T", ctypes.c_double),
+                ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2),
+                ("dpar", ctypes.c_double * 8), ("fpar", ctypes.c_double * 8)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations_max", ctypes.c_int), ("kernel_launches", ctypes.c_int),
+                ("ms_total", ctypes.c_double), ("ms_fine", ctypes.c_double), ("ms_coarse", ctypes.c_double),
+                ("ms_history", ctypes.c_double), ("fine_steps", ctypes.c_double),
+                ("fine_step_modes", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+# name -> (restype, argtypes); the exported symbols of include/psl1.h
+SIGNATURES = {
+    "psl1_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(Instance),
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "psl1_set_D": (ctypes.c_int, [ctypes.c_void_p, _D]),
+    "psl1_set_f": (ctypes.c_int, [ctypes.c_void_p, _D]),
+    "psl1_set_u0": (ctypes.c_int, [ctypes.c_void_p, _D]),
+    "psl1_set_u0_dev": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "psl1_solve_serial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "psl1_solve_parareal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, _I]),
+    "psl1_get_coeffs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D]),
+    "psl1_get_coeffs_dev": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "psl1_get_iterations": (ctypes.c_int, [ctypes.c_void_p, _I]),
+    "psl1_get_errlog": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_int, _I]),
+    "psl1_keep_iterates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "psl1_get_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D]),
+    "psl1_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
+    "psl1_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, _D, _D]),
+    "psl1_fine_slice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D]),
+    "psl1_coarse_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D]),
+    "psl1_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "psl1_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpsl1.so (building it first if needed)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise PSL1Error(-4, f"CUDA library not built: {_build.LIB}")
+        L = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _err(h) -> str:
+    m = load().psl1_last_error(h)
+    return m.decode() if m else ""
+
+
+def _chk(st: int, h):
+    if st != 0:
+        raise PSL1Error(st, _err(h))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def to_instance(s: InstanceSpec) -> Instance:
+    c = Instance()
+    c.dim = s.dim
+    c.modes[0], c.modes[1] = s.modes
+    c.qnodes[0], c.qnodes[1] = s.qnodes
+    c.nsteps, c.alpha, c.T = s.nsteps, s.alpha, s.T
+    c.lo[0], c.lo[1] = s.lo
+    c.hi[0], c.hi[1] = s.hi
+    dp = list(s.dpar) + [0.0] * (8 - len(s.dpar))
+    fp = list(s.fpar) + [0.0] * (8 - len(s.fpar))
+    for i in range(8):
+        c.dpar[i], c.fpar[i] = dp[i], fp[i]
+    return c
+
+
+# ------------------------------------------------------------------ C names
+def psl1_create(specs, P: int, precision: str = "fp64", stream: int | None = None) -> ctypes.c_void_p:
+    arr = (Instance * len(specs))(*[to_instance(s) for s in specs])
+    h = ctypes.c_void_p()
+    _chk(load().psl1_create(ctypes.byref(h), len(specs), arr, int(P), PREC[precision],
+                            ctypes.c_void_p(stream) if stream else None), None)
+    return h
+
+
+def psl1_destroy(h) -> None:
+    load().psl1_destroy(h)
+
+
+class Problem:
+    """A batch of instances on the device (wraps one psl1 handle)."""
+
+    def __init__(self, workload_or_specs, P: int | None = None, precision: str = "fp64",
+                 stream: int | None = None):
+        if isinstance(workload_or_specs, Workload):
+            wl = workload_or_specs
+            self.specs, self.P = list(wl.specs), wl.P
+        else:
+            self.specs, self.P = list(workload_or_specs), int(P)
+        self.K = [s.K for s in self.specs]
+        self.offK = np.concatenate([[0], np.cumsum(self.K)]).astype(np.int64)
+        self.offU = np.concatenate([[0], np.cumsum([(self.P + 1) * k for k in self.K])]).astype(np.int64)
+        self.h = psl1_create(self.specs, self.P, precision, stream)
+        self.L = load()
+        if isinstance(workload_or_specs, Workload):
+            self.set_u0(workload_or_specs.u0_concat())
+
+    def close(self):
+        if self.h:
+            self.L.psl1_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def B(self) -> int:
+        return len(self.specs)
+
+    def set_u0(self, u0):
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        assert u0.size == self.offK[-1]
+        _chk(self.L.psl1_set_u0(self.h, _dp(u0)), self.h)
+
+    def set_u0_dev(self, ptr: int):
+        _chk(self.L.psl1_set_u0_dev(self.h, ctypes.c_void_p(ptr)), self.h)
+
+    def set_D(self, dpar):
+        d = np.ascontiguousarray(dpar, dtype=np.float64).reshape(-1)
+        _chk(self.L.psl1_set_D(self.h, _dp(d)), self.h)
+
+    def set_f(self, fpar):
+        d = np.ascontiguousarray(fpar, dtype=np.float64).reshape(-1)
+        _chk(self.L.psl1_set_f(self.h, _dp(d)), self.h)
+
+    def solve_serial(self, kind: str = "hybrid"):
+        _chk(self.L.psl1_solve_serial(self.h, SERIAL[kind]), self.h)
+
+    def solve_parareal(self, tol: float = 1e-10, max_iter: int = 0, allow_not_converged: bool = False) -> int:
+        it = ctypes.c_int(0)
+        st = self.L.psl1_solve_parareal(self.h, float(tol), int(max_iter), ctypes.byref(it))
+        if st == -6 and allow_not_converged:
+            return it.value
+        _chk(st, self.h)
+        return it.value
+
+    def _split(self, flat) -> list:
+        return [flat[self.offU[b]:self.offU[b + 1]].reshape(self.P + 1, self.K[b]) for b in range(self.B)]
+
+    def get_coeffs(self, which: str = "parareal", flat: bool = False):
+        out = np.zeros(int(self.offU[-1]))
+        _chk(self.L.psl1_get_coeffs(self.h, 0 if which == "parareal" else 1, _dp(out)), self.h)
+        return out if flat else self._split(out)
+
+    def get_coeffs_dev(self, which: str, ptr: int):
+        _chk(self.L.psl1_get_coeffs_dev(self.h, 0 if which == "parareal" else 1, ctypes.c_void_p(ptr)), self.h)
+
+    def get_iterations(self) -> np.ndarray:
+        it = np.zeros(self.B, dtype=np.int32)
+        _chk(self.L.psl1_get_iterations(self.h, it.ctypes.data_as(_I)), self.h)
+        return it
+
+    def get_errlog(self, b: int) -> np.ndarray:
+        n = ctypes.c_int(0)
+        _chk(self.L.psl1_get_errlog(self.h, b, None, 0, ctypes.byref(n)), self.h)
+        out = np.zeros(max(n.value, 1))
+        _chk(self.L.psl1_get_errlog(self.h, b, _dp(out), n.value, ctypes.byref(n)), self.h)
+        return out[: n.value]
+
+    def keep_iterates(self, on: bool = True):
+        _chk(self.L.psl1_keep_iterates(self.h, int(on)), self.h)
+
+    def get_iterate(self, k: int) -> list:
+        out = np.zeros(int(self.offU[-1]))
+        _chk(self.L.psl1_get_iterate(self.h, k, _dp(out)), self.h)
+        return self._split(out)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _chk(self.L.psl1_get_stats(self.h, ctypes.byref(s)), self.h)
+        return s.as_dict()
+
+    def step(self, b: int, c, te: float, mu: float, hist) -> np.ndarray:
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        hist = np.ascontiguousarray(hist, dtype=np.float64)
+        out = np.zeros(self.K[b])
+        _chk(self.L.psl1_step(self.h, b, _dp(c), float(te), float(mu), _dp(hist), _dp(out)), self.h)
+        return out
+
+    def fine_slice(self, b: int, n: int, U) -> np.ndarray:
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        m = self.specs[b].nsteps // self.P
+        V = np.zeros((m + 1, self.K[b]))
+        _chk(self.L.psl1_fine_slice(self.h, b, n, _dp(U), _dp(V)), self.h)
+        return V
+
+    def coarse_step(self, b: int, n: int, U) -> np.ndarray:
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        out = np.zeros(self.K[b])
+        _chk(self.L.psl1_coarse_step(self.h, b, n, _dp(U), _dp(out)), self.h)
+        return out

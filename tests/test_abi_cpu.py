@@ -1,0 +1,54 @@
+"""CPU checks of the C ABI library: it builds, loads, exports every symbol
+declared in include/psl1.h, and refuses to run without a GPU (no fallback)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2510_11023_gb300 import psl1, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(psl1_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = psl1.load()
+    declared = _declared()
+    assert "psl1_solve_parareal" in declared and "psl1_create" in declared
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared <= set(psl1.SIGNATURES), declared - set(psl1.SIGNATURES)
+
+
+def test_invalid_arguments_rejected_before_device_use():
+    L = psl1.load()
+    h = ctypes.c_void_p()
+    st = L.psl1_create(ctypes.byref(h), 0, None, 4, 0, None)
+    assert st == -1
+    wl = workloads.cfg1()
+    arr = (psl1.Instance * 1)(psl1.to_instance(wl.specs[0]))
+    assert L.psl1_create(ctypes.byref(h), 1, arr, 7, 0, None) == -1   # 7 does not divide 256
+    assert b"multiple" in L.psl1_last_error(None)
+    bad = psl1.to_instance(wl.specs[0])
+    bad.alpha = 1.5
+    arr = (psl1.Instance * 1)(bad)
+    assert L.psl1_create(ctypes.byref(h), 1, arr, 8, 0, None) == -1
+
+
+def test_no_cpu_fallback_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(psl1.PSL1Error) as ei:
+        psl1.Problem(workloads.cfg1())
+    assert ei.value.status == -4
