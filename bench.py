@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark: parareal wall time to relative error 1e-8 against the serial
+GPU solve, reported as fine steps x modes per second.
+
+One "step" is one complete parareal solve (coarse sweep, F stages, coarse
+sweeps with correction, stopping test) of the batched 1D workload: 256
+instances with seeded uneven K in [64,256], N = 64 m with m in [16,64]
+(N in [1024,4096]), alpha in {0.3,0.5,0.7,1.0}, P = 64 slices.  The error is
+measured against the sequential fine sweep S_hyb (parareal's fixed point)
+solved on the GPU in plain FP64; the stopping tolerance on the increment is
+picked during warm-up as the loosest one that still reaches 1e-8.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own batch (seed + rank): weak scaling,
+no collective on the data path; rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "parareal wall-time to rel err 1e-8 vs serial GPU solve; fine steps*modes/s"
+UNIT = "fine_steps*modes/s"
+TARGET = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp32"])
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=20251011)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+class Dist:
+    def __init__(self, n_gpus: int, backend: str):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- work accounting
+def step_flops(K: int, hist_terms: int) -> float:
+    """Algorithmic FLOPs of one linearised fine step with K modes, Q = 2K nodes:
+    mirror-folded transforms u (K^2), moments (2K^2), load (K^2) MACs; Cholesky
+    K^3/6 MACs; two triangular solves K^2 MACs; history hist_terms*K MACs."""
+    macs = K**3 / 6.0 + 4.0 * K * K + K * K + hist_terms * K
+    return 2.0 * macs
+
+
+def fstage_flops(wl, iters) -> float:
+    """FLOPs of all F-stage launches of one parareal solve (slices n >= k at iteration k)."""
+    tot = 0.0
+    for b, s in enumerate(wl.specs):
+        K, m = s.K, s.nsteps // wl.P
+        per_r = sum(r - 1 for r in range(1, m + 1))
+        for k in range(int(iters[b])):
+            for n in range(k, wl.P):
+                tot += m * step_flops(K, 0) + 2.0 * K * (per_r + m * n)
+    return tot
+
+
+def rel_err(U, S) -> float:
+    """max over instances of max_n ||U_n - S_n||_2 / max_n ||S_n||_2."""
+    return max(float(np.sqrt(((u - s) ** 2).sum(1)).max() / np.sqrt((s**2).sum(1)).max()) for u, s in zip(U, S))
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_prob(spec, P):
+    import oracle as O
+    return O.make_prob(dim=spec.dim, Mx=spec.modes[0], My=spec.modes[1], Qx=spec.qnodes[0] or None,
+                       Qy=spec.qnodes[1] or None, N=spec.nsteps, P=P, alpha=spec.alpha, T=spec.T,
+                       lo=spec.lo, hi=spec.hi, dpar=spec.dpar, fpar=spec.fpar)
+
+
+def oracle_throughput(wl, S, seconds: float) -> tuple:
+    """The FP64 oracle (single thread) on a bounded sample of the workload:
+    fine propagators of the middle slice of successive instances (history from
+    S, or from the oracle's coarse sweep), until `seconds` of CPU time are spent."""
+    import oracle as O
+    O.build()
+    n = wl.P // 2
+    work, t0, inst = 0.0, time.perf_counter(), 0
+    while time.perf_counter() - t0 < seconds and inst < wl.B:
+        s = wl.specs[inst]
+        op = oracle_prob(s, wl.P)
+        U = S[inst][: n + 1] if S is not None else O.coarse_sweep(op, wl.u0[inst])[: n + 1]
+        O.fine_slice(op, n, U, diff_form=True)
+        work += (s.nsteps // wl.P) * s.K
+        inst += 1
+    dt = time.perf_counter() - t0
+    return work / dt, dt, inst
+
+
+def reference_arm(args, dist: Dist):
+    from paper_2510_11023_gb300 import workloads
+    if dist.rank != 0:
+        return
+    wl = workloads.cfg2(B=args.batch, seed=args.seed)
+    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_throughput(wl, None, per_step / 4)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, dt, ninst = oracle_throughput(wl, None, per_step)
+        vals.append(v)
+        secs.append(dt)
+    v = float(np.mean(vals))
+    sample = (f"oracle fine propagator F_n (n = P/2, coarse-sweep history) of successive instances of the "
+              f"batched workload, ~{per_step:.0f} s per step, 1 thread")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "batch": wl.B, "P": wl.P},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        dist = Dist(args.gpus, "gloo")
+        reference_arm(args, dist)
+        dist.close()
+        return
+    import torch
+    from paper_2510_11023_gb300 import psl1, workloads
+
+    dist = Dist(args.gpus, "nccl")
+    torch.cuda.set_device(dist.local)
+    stream = torch.cuda.current_stream()
+    psl1.load()
+    fp64_tf, fp32_tf = psl1.psl1_probe_peaks()
+
+    wl = workloads.cfg2(B=args.batch, seed=args.seed + dist.rank)
+    u0 = wl.u0_concat()
+    d_u0 = torch.from_numpy(u0).to("cuda")
+    torch.cuda.synchronize()
+
+    # plain serial FP64 GPU solve S_hyb: the reference solution and the baseline time
+    ref = psl1.Problem(wl, precision="fp64", stream=stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ref.solve_serial("hybrid")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    serial_fp64_ms = e0.elapsed_time(e1)
+    S = ref.get_coeffs("serial")
+    ref.close()
+
+    pr = psl1.Problem(wl, precision=args.precision, stream=stream.cuda_stream)
+    if args.precision != "fp64":
+        e0.record(stream)
+        pr.solve_serial("hybrid")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        serial_ms = e0.elapsed_time(e1)
+    else:
+        serial_ms = serial_fp64_ms
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    # warm-up: pick the stopping tolerance that reaches the target error
+    tol, err = 1e-8, None
+    for w in range(max(args.warmup, 1)):
+        pr.set_u0_dev(d_u0.data_ptr())
+        pr.solve_parareal(tol=tol, allow_not_converged=True)
+        err = rel_err(pr.get_coeffs("parareal"), S)
+        while err > TARGET and tol > 1e-13:
+            tol /= 3.0
+            pr.solve_parareal(tol=tol, allow_not_converged=True)
+            err = rel_err(pr.get_coeffs("parareal"), S)
+
+    # timed region
+    dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dist.local)
+    clk.start()
+    times, fine_ms, fine_launches, flops, launches, iters_all = [], 0.0, 0, 0.0, 0, []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        pr.set_u0_dev(d_u0.data_ptr())
+        e0.record(stream)
+        pr.solve_parareal(tol=tol, allow_not_converged=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        st = pr.stats()
+        its = pr.get_iterations()
+        iters_all.append(int(its.max()))
+        fine_ms += st["ms_fine"]
+        fine_launches += st["iterations_max"]
+        launches += st["kernel_launches"]
+        flops += fstage_flops(wl, its)
+    torch.cuda.synchronize()
+    dist.barrier()
+    wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    err = rel_err(pr.get_coeffs("parareal"), S)
+
+    ms_step = dist.max(float(np.mean(times)))
+    useful = float(sum(s.nsteps * s.K for s in wl.specs))
+    value = dist.sum(useful) / (ms_step * 1e-3)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_out = np.zeros(int(pr.offU[-1]))
+        et = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pr.set_u0(u0)
+            pr.solve_parareal(tol=tol, allow_not_converged=True)
+            pr.L.psl1_get_coeffs(pr.h, 0, h_out.ctypes.data_as(psl1._D))
+            et.append(time.perf_counter() - t0)
+        e_ms = dist.max(1e3 * float(np.mean(et)))
+        e2e = {"value": dist.sum(useful) / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(u0.nbytes),
+               "d2h_bytes_per_step": int(h_out.nbytes)}
+
+    # roofline of the dominant kernel (F stage), ALU-bound
+    fine_avg_ms = fine_ms / max(fine_launches, 1)
+    achieved = flops / max(fine_launches, 1) / (fine_avg_ms * 1e-3) / 1e12
+    peak = fp64_tf if args.precision == "fp64" else fp32_tf
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_fstage",
+            "peak_source": ("measured FP64 FMA throughput (psl1_probe_peaks)" if args.precision == "fp64"
+                            else "measured FP32 FMA throughput (psl1_probe_peaks)")}
+
+    cpu = None
+    if not args.no_cpu and dist.rank == 0 and dist.world == 1:
+        v, dt, ninst = oracle_throughput(wl, S, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 oracle fine propagator F_n at n = P/2 of the first {ninst} instances "
+                         f"({dt:.1f} s, history from the GPU serial solve)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "batch": wl.B, "P": wl.P, "precision": args.precision,
+                       "l2": "flushed (256 MB write) before every timed step", "seed": args.seed},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "rel_err_vs_serial_fp64": err, "stop_tol": tol, "iterations": iters_all,
+            "serial_fp64_ms": serial_fp64_ms, "serial_ms": serial_ms,
+            "speedup_vs_serial_fp64": serial_fp64_ms / ms_step, "speedup_vs_serial_same_precision": serial_ms / ms_step,
+            "measured_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf}, "wall_s": wall}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    pr.close()
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -171,6 +171,12 @@ psl1_status psl1_fine_slice(psl1_h h, int b, int n, const double* U, double* V);
 /* Coarse propagator G_n of instance b on U_0..U_n (host); out: K_b doubles. */
 psl1_status psl1_coarse_step(psl1_h h, int b, int n, const double* U, double* out);
 
+/* ---- measurement utility (no counterpart in the paper) ------------------ */
+/* Measured FP64 and FP32 FMA throughput of the current device in TFLOP/s
+ * (dependent FMA chains on every SM, best of three timed launches).  Used
+ * as the roofline denominators of the ALU-bound kernels.                    */
+psl1_status psl1_probe_peaks(double* fp64_tflops, double* fp32_tflops);
+
 const char* psl1_last_error(psl1_h h);
 void psl1_destroy(psl1_h h);
 

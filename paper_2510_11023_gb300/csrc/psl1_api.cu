@@ -11,7 +11,7 @@
 #include <tuple>
 #include <vector>
 
-#include "../../include/psl1.h"
+#include "psl1.h"
 #include "psl1_kernels.h"
 
 using namespace psl1;
@@ -175,8 +175,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     *out = nullptr;
     if (batch < 1 || !in) return fail(nullptr, PSL1_ERR_ARG, "batch must be >= 1 with an instance array");
     if (P < 1) return fail(nullptr, PSL1_ERR_ARG, "P must be >= 1");
-    if (precision != PSL1_PREC_FP64)
-        return fail(nullptr, PSL1_ERR_ARG, "precision %d is not available in this build", precision);
+    if (precision != PSL1_PREC_FP64 && precision != PSL1_PREC_MIXED && precision != PSL1_PREC_FP32)
+        return fail(nullptr, PSL1_ERR_ARG, "unknown precision %d", precision);
     for (int b = 0; b < batch; ++b) TRY(validate(in[b], P, b));
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -262,6 +262,12 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
             o += (long long)t.Qh * t.Mx;
             t.oC = o;
             o += (long long)t.Qh * (2 * t.Mx + 1);
+            t.oStd = o;
+            o += (long long)t.Mx * t.Qh;
+            t.oSd = o;
+            o += (long long)t.Qh * t.Mx;
+            t.oCd = o;
+            o += (long long)t.Qh * (2 * t.Mx + 1);
             h->tabElems = o;
             int id = (int)h->tabs.size();
             h->tabs.push_back(t);
@@ -295,6 +301,15 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     }
     int nbmax = h->Kpmax / TILE;
     int nslots = std::max(2 * h->nsm, batch);
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int fac_in_smem = 0;
+    SmemLayout lay = make_layout(precision, h->Kmax, h->Kpmax, h->Qhmax, max_smem - 1024, &fac_in_smem);
+    if (lay.total > max_smem - 1024) {
+        g_create_error = "instance too large for the shared-memory layout";
+        psl1_destroy(h);
+        return PSL1_ERR_ARG;
+    }
     CTRY(dalloc(h, &h->d_inst, batch));
     CTRY(dalloc(h, &h->d_tab, h->tabs.size()));
     CTRY(dalloc(h, &h->d_tp, h->tabElems));
@@ -310,7 +325,10 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     CTRY(dalloc(h, &h->d_active, batch));
     CTRY(dalloc(h, &h->d_counter, 1));
     CTRY(dalloc(h, &h->d_status, 1));
-    long long work_stride = bp_elems(nbmax, TILE);
+    // per-slot factor workspace: FP64 factor, or the FP32 factor when it does not fit in shared memory
+    long long work_stride = precision == PSL1_PREC_FP64 ? bp_elems(nbmax, TILE)
+                            : fac_in_smem                ? 1
+                                                         : (bp_elems(nbmax, MIX_LDB) + 1) / 2;
     long long ring_stride = (long long)h->mmax * h->Kmax;
     CTRY(dalloc(h, &h->d_work, (size_t)nslots * work_stride));
     CTRY(dalloc(h, &h->d_ring, (size_t)nslots * ring_stride));
@@ -333,6 +351,9 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         jobs[t].St = h->d_tp + T.oSt;
         jobs[t].S = h->d_tp + T.oS;
         jobs[t].C = h->d_tp + T.oC;
+        jobs[t].Std = h->d_tp + T.oStd;
+        jobs[t].Sd = h->d_tp + T.oSd;
+        jobs[t].Cd = h->d_tp + T.oCd;
     }
     auto cu = [&](cudaError_t e2, const char* what) -> psl1_status {
         if (e2 != cudaSuccess) return fail(h, PSL1_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e2));
@@ -369,6 +390,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.Qhmax = h->Qhmax;
     a.mmax = h->mmax;
     a.prec = precision;
+    a.L = lay;
+    a.fac_in_smem = fac_in_smem;
     h->iters.assign(batch, 0);
     h->errlog.assign(batch, {});
     h->d_Ucur = h->d_Ua;

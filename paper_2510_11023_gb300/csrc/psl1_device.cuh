@@ -16,6 +16,7 @@ namespace psl1 {
 constexpr int NT = 256;          // threads per CTA of the step kernels
 constexpr int KMAX_1D = 512;     // largest 1D mode count handled by one CTA
 constexpr int TILE = 32;         // Cholesky block size (one warp per panel)
+constexpr int MIX_LDB = 33;      // padded row stride of FP32 factor blocks (bank-conflict free)
 
 // elements of a block-packed lower triangle of nb x nb blocks with row stride ldb
 __host__ __device__ constexpr int bp_elems(int nb, int ldb) { return nb * (nb + 1) / 2 * TILE * ldb; }
@@ -47,6 +48,7 @@ struct TabDev {
     long long oSt;   // Mx x Qh : phi_k(x_q)      (row k, coalesced over q)
     long long oS;    // Qh x Mx : phi_k(x_q)      (row q, coalesced over k)
     long long oC;    // Qh x (2Mx+1) : cos(s pi (x_q - lo)/L)
+    long long oStd, oSd, oCd;   // the same three tables as double-float pairs
 };
 
 // Device error word: the first failure wins.  code < 0 is a psl1_status.

@@ -12,46 +12,103 @@
 //                   kernel over all instances plus one step CTA per instance.
 #include "psl1_kernels.h"
 #include "psl1_step.cuh"
+#include "psl1_step_mixed.cuh"
 
 namespace psl1 {
 
 struct Carve {
     double *cur, *hist, *nxt, *F;
     StepSmem s;
+    MixSmem ms;
+    float* fac;
 };
+
+template <typename T>
+__device__ __forceinline__ T* at(char* base, int off)
+{
+    return off >= 0 ? reinterpret_cast<T*>(base + off) : nullptr;
+}
 
 __device__ __forceinline__ Carve carve(const PathArgs& a, char* base)
 {
-    double* p = reinterpret_cast<double*>(base);
+    const SmemLayout& L = a.L;
     Carve c;
-    c.cur = p;
-    p += a.Kmax;
-    c.hist = p;
-    p += a.Kmax;
-    c.nxt = p;
-    p += a.Kmax;
-    c.F = p;
-    p += a.Kmax;
-    c.s.v = p;
-    p += a.Kpmax;
-    c.s.wp = p;
-    p += a.Qhmax;
-    c.s.wm = p;
-    p += a.Qhmax;
-    c.s.fp = p;
-    p += a.Qhmax;
-    c.s.fm = p;
-    p += a.Qhmax;
-    c.s.g = p;
-    p += 2 * a.Kmax + 1;
-    c.s.bad = reinterpret_cast<int*>(p);
+    c.cur = at<double>(base, L.cur);
+    c.hist = at<double>(base, L.hist);
+    c.nxt = at<double>(base, L.nxt);
+    c.F = at<double>(base, L.F);
+    c.s.v = at<double>(base, L.v);
+    c.s.wp = at<double>(base, L.wp);
+    c.s.wm = at<double>(base, L.wm);
+    c.s.fp = at<double>(base, L.fp);
+    c.s.fm = at<double>(base, L.fm);
+    c.s.g = at<double>(base, L.g);
+    c.s.bad = at<int>(base, L.bad);
+    c.ms.cdf = at<df>(base, L.cdf);
+    c.ms.wpd = at<df>(base, L.wpd);
+    c.ms.wmd = at<df>(base, L.wmd);
+    c.ms.fpd = at<df>(base, L.fpd);
+    c.ms.fmd = at<df>(base, L.fmd);
+    c.ms.gdf = at<df>(base, L.gdf);
+    c.ms.ydf = at<df>(base, L.ydf);
+    c.ms.x = at<double>(base, L.x);
+    c.ms.rhs = at<double>(base, L.rhs);
+    c.ms.z = at<float>(base, L.z);
+    c.ms.red = at<float>(base, L.red);
+    c.ms.flag = c.s.bad;
+    c.fac = a.fac_in_smem ? at<float>(base, L.fac)
+                          : reinterpret_cast<float*>(a.work + (size_t)blockIdx.x * a.work_stride);
     return c;
 }
 
-size_t step_smem_bytes(const PathArgs& a)
+// Shared-memory layout.  Regions are 16-byte aligned; the FP32 factor goes
+// last and is placed in shared memory only if the whole layout fits.
+SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem)
 {
-    return sizeof(double) * (size_t)(4 * a.Kmax + a.Kpmax + 4 * a.Qhmax + 2 * a.Kmax + 1) + 16;
+    SmemLayout L;
+    int off = 0;
+    auto take = [&](size_t bytes) {
+        int o = off;
+        off += (int)((bytes + 15) / 16 * 16);
+        return o;
+    };
+    const bool f64 = prec == 0;
+    L.cur = take(8 * (size_t)Kmax);
+    L.hist = take(8 * (size_t)Kmax);
+    L.nxt = take(8 * (size_t)Kmax);
+    L.F = take(8 * (size_t)Kmax);
+    L.v = f64 ? take(8 * (size_t)Kpmax) : -1;
+    L.wp = f64 ? take(8 * (size_t)Qhmax) : -1;
+    L.wm = f64 ? take(8 * (size_t)Qhmax) : -1;
+    L.fp = f64 ? take(8 * (size_t)Qhmax) : -1;
+    L.fm = f64 ? take(8 * (size_t)Qhmax) : -1;
+    L.g = f64 ? take(8 * (size_t)(2 * Kmax + 1)) : -1;
+    L.bad = take(16);
+    L.cdf = f64 ? -1 : take(8 * (size_t)Kmax);
+    L.wpd = f64 ? -1 : take(8 * (size_t)Qhmax);
+    L.wmd = f64 ? -1 : take(8 * (size_t)Qhmax);
+    L.fpd = f64 ? -1 : take(8 * (size_t)Qhmax);
+    L.fmd = f64 ? -1 : take(8 * (size_t)Qhmax);
+    L.gdf = f64 ? -1 : take(8 * (size_t)(2 * Kmax + 1));
+    L.ydf = f64 ? -1 : take(8 * (size_t)Kmax);
+    L.x = f64 ? -1 : take(8 * (size_t)Kpmax);
+    L.rhs = f64 ? -1 : take(8 * (size_t)Kpmax);
+    L.z = f64 ? -1 : take(4 * (size_t)Kpmax);
+    L.red = f64 ? -1 : take(4 * (NT / 32));
+    L.fac = -1;
+    *fac_in_smem = 0;
+    if (!f64) {
+        size_t fb = 4 * (size_t)bp_elems(Kpmax / TILE, MIX_LDB);
+        if (off + fb <= (size_t)max_smem) {
+            L.fac = take(fb);
+            *fac_in_smem = 1;
+        }
+    }
+    L.total = off;
+    return L;
 }
+
+size_t step_smem_bytes(const PathArgs& a) { return (size_t)a.L.total; }
 
 enum { WHERE_FINE = 1, WHERE_COARSE = 2, WHERE_UNI = 3, WHERE_ONE = 4 };
 
@@ -59,8 +116,12 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
                                        const double* hist, double te, double mu, double* out, Carve& cv)
 {
     const TabDev& Tb = a.tab[I.tab];
-    BPack<double, TILE> A{a.work + (size_t)blockIdx.x * a.work_stride};
-    return step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
+    if (a.prec == 0) {
+        BPack<double, TILE> A{a.work + (size_t)blockIdx.x * a.work_stride};
+        return step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
+    }
+    BPack<float, MIX_LDB> A{cv.fac};
+    return step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s, cv.ms, a.prec == 2);
 }
 
 __device__ __forceinline__ void check_finite(const PathArgs& a, const double* v, int K, int ii, int where,

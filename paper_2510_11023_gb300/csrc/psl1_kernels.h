@@ -10,6 +10,14 @@ struct TableJob {
     int Mx, Qh;
     double lo, hi;
     double *xh, *wh, *St, *S, *C, *aux;
+    double *Std, *Sd, *Cd;   // double-float copies (float pairs stored in 8-byte slots)
+};
+
+// Byte offsets of the per-CTA shared-memory regions (host-computed; -1 = absent).
+struct SmemLayout {
+    int cur, hist, nxt, F, v, wp, wm, fp, fm, g, bad;     // FP64 path (+ common)
+    int cdf, wpd, wmd, fpd, fmd, gdf, ydf, x, rhs, z, red, fac;   // FP32-pipe path
+    int total;
 };
 
 // Pointers and sizes every solver kernel needs.
@@ -26,7 +34,11 @@ struct PathArgs {
     int nslots;              // slots available in work/ring
     int Kmax, Kpmax, Qhmax, mmax;
     int prec;                // PSL1_PREC_*
+    SmemLayout L;            // shared-memory layout of the step kernels
+    int fac_in_smem;         // FP32 factor in shared memory (else in the work slot)
 };
+
+SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem);
 
 size_t step_smem_bytes(const PathArgs& a);
 

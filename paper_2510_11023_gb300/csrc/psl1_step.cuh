@@ -36,6 +36,29 @@ __device__ __forceinline__ double D_eval(const InstDev& I, double sx1, double sx
     return v * X0;
 }
 
+// FP32 versions (PSL1_PREC_FP32)
+__device__ __forceinline__ float D_eval32(const InstDev& I, float sx1, float sx2, float u)
+{
+    const double* c = I.dpar;
+    float X0 = 1.0f + (float)c[4] * sx2;
+    float X1 = 1.0f + (float)c[6] * sx2;
+    float v = (float)c[0] + (float)c[3] * sx1;
+    if (c[1] != 0.0) v += (float)c[1] / (1.0f + u * u) * X1;
+    if (c[2] != 0.0) v += (float)c[2] * u;
+    return v * X0;
+}
+
+__device__ __forceinline__ float f_eval32(const InstDev& I, float sx1, float t, float u)
+{
+    const double* c = I.fpar;
+    float v = 0.0f;
+    if (c[0] != 0.0) v += (float)c[0] * cosf(u);
+    if (c[1] != 0.0) v += (float)c[1] * sinf(u);
+    if (c[2] != 0.0) v += (float)c[2] * u * (1.0f - u);
+    if (c[3] != 0.0) v += (float)c[3] * sx1 * expf(-t);
+    return v;
+}
+
 // manufactured source for u = (1 + t^a) sin(pi x), D = d0 + d1/(1+u^2)
 __device__ double src1_eval(const InstDev& I, double x, double sx1, double t)
 {

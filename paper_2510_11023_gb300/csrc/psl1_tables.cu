@@ -47,7 +47,7 @@ __global__ void k_gauss_legendre_half(int Q, double lo, double hi, double* xh, d
 // C[q][s] = cos(s pi th_q), th_q = (x_q - lo)/L, and the node functions of the
 // coefficient families at x_q and its mirror.
 __global__ void k_basis_tables(int Mx, int Qh, double lo, double hi, const double* xh, double* St,
-                               double* S, double* C, double* aux)
+                               double* S, double* C, double* aux, df* Std, df* Sd, df* Cd)
 {
     int q = blockIdx.x;
     if (q >= Qh) return;
@@ -58,8 +58,14 @@ __global__ void k_basis_tables(int Mx, int Qh, double lo, double hi, const doubl
         double v = sc * sinpi(k * th);
         St[(size_t)(k - 1) * Qh + q] = v;
         S[(size_t)q * Mx + (k - 1)] = v;
+        Std[(size_t)(k - 1) * Qh + q] = df_from_double(v);
+        Sd[(size_t)q * Mx + (k - 1)] = df_from_double(v);
     }
-    for (int s = threadIdx.x; s <= 2 * Mx; s += blockDim.x) C[(size_t)q * (2 * Mx + 1) + s] = cospi(s * th);
+    for (int s = threadIdx.x; s <= 2 * Mx; s += blockDim.x) {
+        double v = cospi(s * th);
+        C[(size_t)q * (2 * Mx + 1) + s] = v;
+        Cd[(size_t)q * (2 * Mx + 1) + s] = df_from_double(v);
+    }
     if (threadIdx.x == 0) {
         double xa = xh[q], xb = lo + hi - xh[q];
         aux[4 * q + 0] = sinpi(xa);
@@ -105,7 +111,8 @@ cudaError_t launch_tables(const TableJob& job, cudaStream_t s)
     int Q = 2 * job.Qh;
     k_gauss_legendre_half<<<(Q + 127) / 128, 128, 0, s>>>(Q, job.lo, job.hi, job.xh, job.wh);
     k_basis_tables<<<job.Qh, 128, 0, s>>>(job.Mx, job.Qh, job.lo, job.hi, job.xh, job.St, job.S, job.C,
-                                          job.aux);
+                                          job.aux, reinterpret_cast<df*>(job.Std), reinterpret_cast<df*>(job.Sd),
+                                          reinterpret_cast<df*>(job.Cd));
     return cudaGetLastError();
 }
 

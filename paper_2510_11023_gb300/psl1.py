@@ -71,6 +71,7 @@ SIGNATURES = {
     "psl1_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, _D, _D]),
     "psl1_fine_slice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D]),
     "psl1_coarse_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D]),
+    "psl1_probe_peaks": (ctypes.c_int, [_D, _D]),
     "psl1_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "psl1_destroy": (None, [ctypes.c_void_p]),
 }
@@ -133,6 +134,13 @@ def psl1_create(specs, P: int, precision: str = "fp64", stream: int | None = Non
     _chk(load().psl1_create(ctypes.byref(h), len(specs), arr, int(P), PREC[precision],
                             ctypes.c_void_p(stream) if stream else None), None)
     return h
+
+
+def psl1_probe_peaks() -> tuple:
+    """Measured (FP64, FP32) FMA throughput of the current device, TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _chk(load().psl1_probe_peaks(ctypes.byref(a), ctypes.byref(b)), None)
+    return a.value, b.value
 
 
 def psl1_destroy(h) -> None:
