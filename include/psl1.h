@@ -168,6 +168,29 @@ psl1_status psl1_step(psl1_h h, int b, const double* c_prev, double t_e, double 
  * (n+1) K_b doubles); V receives U_{n,0..m} ((m+1) K_b doubles).           */
 psl1_status psl1_fine_slice(psl1_h h, int b, int n, const double* U, double* V);
 
+/* Allocation-free fine propagator (the paper has no counterpart; this is a
+ * service to callers).  Same result as psl1_fine_slice, but the inputs and
+ * outputs are device arrays the caller owns (d_U: (n+1) K_b doubles,
+ * d_V: (m+1) K_b doubles) and the call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.  It is meant for callers that
+ * cannot allocate device memory at the time they call -- for example a
+ * real-time loop whose device memory was all planned before it started,
+ * or code running under a memory manager that forbids new allocations --
+ * after creating the handle where allocation was still allowed.
+ * Scratch (the fine-history ring of m K_b doubles plus, for PSL1_PREC_FP64 or
+ * a factor too large for shared memory, the factor workspace) comes from one
+ * fixed 4 MiB device array compiled into the library, which every device that
+ * loads the library keeps until the process exits.  Instances whose scratch
+ * exceeds 4 MiB are rejected with PSL1_ERR_ARG (the message gives the need).
+ * The first call on a device looks up that array's device address (with the
+ * device current), so make the first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents; every element
+ * is written before it is read, so nothing needs clearing, but calls that
+ * overlap on the GPU (for instance from two handles on different streams)
+ * race.  Ordered on the handle's stream; returns after the kernel finished,
+ * with device-side failures reported as in psl1_fine_slice.                */
+psl1_status psl1_fine_slice_noalloc(psl1_h h, int b, int n, const double* d_U, double* d_V);
+
 /* Coarse propagator G_n of instance b on U_0..U_n (host); out: K_b doubles. */
 psl1_status psl1_coarse_step(psl1_h h, int b, int n, const double* U, double* out);
 

@@ -709,6 +709,25 @@ psl1_status psl1_fine_slice(psl1_h h, int b, int n, const double* U, double* V)
     return check_device_status(h);
 }
 
+psl1_status psl1_fine_slice_noalloc(psl1_h h, int b, int n, const double* d_U, double* d_V)
+{
+    if (!h || !d_U || !d_V || b < 0 || b >= h->B || n < 0 || n >= h->P)
+        return fail(h, PSL1_ERR_ARG, "bad argument");
+    const InstDev& I = h->inst[b];
+    long long ring = (long long)I.m * I.K;
+    long long work = h->prec == PSL1_PREC_FP64 ? bp_elems(I.nb, TILE)
+                     : h->pa.fac_in_smem        ? 0
+                                                : (bp_elems(I.nb, MIX_LDB) + 1) / 2;
+    if (ring + work > NOALLOC_SCRATCH_DOUBLES)
+        return fail(h, PSL1_ERR_ARG,
+                    "instance %d needs %lld doubles of scratch (m*K = %lld plus factor %lld); the fixed "
+                    "allocation-free array holds %lld",
+                    b, ring + work, ring, work, NOALLOC_SCRATCH_DOUBLES);
+    TRY(reset_status(h));
+    CU(h, launch_one_slice_noalloc(h->pa, b, n, d_U, d_V, ring, work, h->stream));
+    return check_device_status(h);
+}
+
 psl1_status psl1_coarse_step(psl1_h h, int b, int n, const double* U, double* out)
 {
     if (!h || !U || !out || b < 0 || b >= h->B || n < 0 || n >= h->P) return fail(h, PSL1_ERR_ARG, "bad argument");

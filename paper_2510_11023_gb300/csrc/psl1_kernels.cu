@@ -391,6 +391,56 @@ __global__ void __launch_bounds__(NT) k_one_coarse(PathArgs a, int ii, int n, co
     for (int k = threadIdx.x; k < I.K; k += NT) out[k] = cv.nxt[k];
 }
 
+// ------------------------------------------------------------------ allocation-free slice
+// For callers that must not allocate device memory while they run (a real-time
+// loop whose memory was planned up front, or code running under an allocator
+// that forbids new device allocations): the single-slice fine propagator with
+// its scratch -- the fine-history ring and, where the factor does not sit in
+// shared memory, the factor workspace -- taken from this fixed array instead of
+// the handle's per-slot pools.  Every element of the scratch is written before
+// it is read, so nothing has to be cleared between calls; all calls share the
+// array, so calls that overlap on the GPU race.
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+
+__global__ void __launch_bounds__(NT) k_one_slice_noalloc(PathArgs a, int ii, int n, const double* U, double* V)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve(a, smem_raw);
+    const InstDev& I = a.inst[ii];
+    fine_slice(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring);
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+double* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+cudaError_t launch_one_slice_noalloc(const PathArgs& a, int b, int n, const double* U, double* V,
+                                     long long ring_doubles, long long work_doubles, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_noalloc_addr[dev]) {   // once per device, with that device current
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    PathArgs a2 = a;
+    a2.ring = g_noalloc_addr[dev];
+    a2.ring_stride = ring_doubles;
+    a2.work = g_noalloc_addr[dev] + ring_doubles;
+    a2.work_stride = work_doubles;
+    a2.nslots = 1;
+    size_t sm = step_smem_bytes(a2);
+    e = cudaFuncSetAttribute(k_one_slice_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_one_slice_noalloc<<<1, NT, sm, s>>>(a2, b, n, U, V);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename Kern>
 static cudaError_t prep(Kern k, size_t smem)

@@ -65,4 +65,9 @@ cudaError_t launch_one_step(const PathArgs& a, int b, const double* c, const dou
 cudaError_t launch_one_slice(const PathArgs& a, int b, int n, const double* U, double* V, cudaStream_t s);
 cudaError_t launch_one_coarse(const PathArgs& a, int b, int n, const double* U, double* out, cudaStream_t s);
 
+// Single slice with scratch from a fixed device array (no allocation).
+constexpr long long NOALLOC_SCRATCH_DOUBLES = 512 * 1024;   // 4 MiB
+cudaError_t launch_one_slice_noalloc(const PathArgs& a, int b, int n, const double* U, double* V,
+                                     long long ring_doubles, long long work_doubles, cudaStream_t s);
+
 }  // namespace psl1

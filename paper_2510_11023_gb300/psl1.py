@@ -71,6 +71,8 @@ SIGNATURES = {
     "psl1_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, _D, _D]),
     "psl1_fine_slice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D]),
     "psl1_coarse_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D]),
+    "psl1_fine_slice_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
     "psl1_probe_peaks": (ctypes.c_int, [_D, _D]),
     "psl1_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "psl1_destroy": (None, [ctypes.c_void_p]),
@@ -262,6 +264,10 @@ class Problem:
         V = np.zeros((m + 1, self.K[b]))
         _chk(self.L.psl1_fine_slice(self.h, b, n, _dp(U), _dp(V)), self.h)
         return V
+
+    def fine_slice_noalloc(self, b: int, n: int, d_U: int, d_V: int) -> None:
+        """F_n on caller-owned device arrays (pointers), without any allocation."""
+        _chk(self.L.psl1_fine_slice_noalloc(self.h, b, n, ctypes.c_void_p(d_U), ctypes.c_void_p(d_V)), self.h)
 
     def coarse_step(self, b: int, n: int, U) -> np.ndarray:
         U = np.ascontiguousarray(U, dtype=np.float64)
