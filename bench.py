@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--reference", default="fp64", choices=["fp64", "same"],
+                    help="precision of the serial S_hyb the error is measured against (same: profiling runs)")
     return ap.parse_args()
 
 
@@ -238,7 +240,8 @@ def main():
     torch.cuda.synchronize()
 
     # plain serial FP64 GPU solve S_hyb: the reference solution and the baseline time
-    ref = psl1.Problem(wl, precision="fp64", stream=stream.cuda_stream)
+    ref = psl1.Problem(wl, precision="fp64" if args.reference == "fp64" else args.precision,
+                       stream=stream.cuda_stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     ref.solve_serial("hybrid")
