@@ -304,7 +304,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int fac_in_smem = 0;
-    SmemLayout lay = make_layout(precision, h->Kmax, h->Kpmax, h->Qhmax, max_smem - 1024, &fac_in_smem);
+    const int inner = INNER_PCG;
+    SmemLayout lay = make_layout(precision, inner, h->Kmax, h->Kpmax, h->Qhmax, max_smem - 1024, &fac_in_smem);
     if (lay.total > max_smem - 1024) {
         g_create_error = "instance too large for the shared-memory layout";
         psl1_destroy(h);
@@ -327,7 +328,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     CTRY(dalloc(h, &h->d_status, 1));
     // per-slot factor workspace: FP64 factor, or the FP32 factor when it does not fit in shared memory
     long long work_stride = precision == PSL1_PREC_FP64 ? bp_elems(nbmax, TILE)
-                            : fac_in_smem                ? 1
+                            : (fac_in_smem || inner == INNER_PCG) ? 1
                                                          : (bp_elems(nbmax, MIX_LDB) + 1) / 2;
     long long ring_stride = (long long)h->mmax * h->Kmax;
     CTRY(dalloc(h, &h->d_work, (size_t)nslots * work_stride));
@@ -392,6 +393,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.prec = precision;
     a.L = lay;
     a.fac_in_smem = fac_in_smem;
+    a.inner = inner;
     h->iters.assign(batch, 0);
     h->errlog.assign(batch, {});
     h->d_Ucur = h->d_Ua;
@@ -716,7 +718,7 @@ psl1_status psl1_fine_slice_noalloc(psl1_h h, int b, int n, const double* d_U, d
     const InstDev& I = h->inst[b];
     long long ring = (long long)I.m * I.K;
     long long work = h->prec == PSL1_PREC_FP64 ? bp_elems(I.nb, TILE)
-                     : h->pa.fac_in_smem        ? 0
+                     : (h->pa.fac_in_smem || h->pa.inner == INNER_PCG) ? 0
                                                 : (bp_elems(I.nb, MIX_LDB) + 1) / 2;
     if (ring + work > NOALLOC_SCRATCH_DOUBLES)
         return fail(h, PSL1_ERR_ARG,

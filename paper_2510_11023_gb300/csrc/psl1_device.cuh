@@ -16,6 +16,8 @@ namespace psl1 {
 constexpr int NT = 256;          // threads per CTA of the step kernels
 constexpr int KMAX_1D = 512;     // largest 1D mode count handled by one CTA
 constexpr int TILE = 32;         // Cholesky block size (one warp per panel)
+constexpr int INNER_CHOL = 0;    // FP32 inner solver of the refinement: blocked Cholesky
+constexpr int INNER_PCG = 1;     //                                      Jacobi-preconditioned CG
 constexpr int MIX_LDB = 33;      // padded row stride of FP32 factor blocks (bank-conflict free)
 
 // elements of a block-packed lower triangle of nb x nb blocks with row stride ldb

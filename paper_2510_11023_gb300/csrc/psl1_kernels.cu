@@ -20,6 +20,7 @@ struct Carve {
     double *cur, *hist, *nxt, *F;
     StepSmem s;
     MixSmem ms;
+    PcgSmem cg;
     float* fac;
 };
 
@@ -56,6 +57,13 @@ __device__ __forceinline__ Carve carve(const PathArgs& a, char* base)
     c.ms.z = at<float>(base, L.z);
     c.ms.red = at<float>(base, L.red);
     c.ms.flag = c.s.bad;
+    c.cg.x = at<float>(base, L.cgx);
+    c.cg.r = at<float>(base, L.cgr);
+    c.cg.p = at<float>(base, L.cgp);
+    c.cg.q = at<float>(base, L.cgq);
+    c.cg.pl = at<float>(base, L.cgpl);
+    c.cg.dinv = at<float>(base, L.cgdinv);
+    c.cg.red2 = at<float>(base, L.cgred);
     c.fac = a.fac_in_smem ? at<float>(base, L.fac)
                           : reinterpret_cast<float*>(a.work + (size_t)blockIdx.x * a.work_stride);
     return c;
@@ -63,7 +71,7 @@ __device__ __forceinline__ Carve carve(const PathArgs& a, char* base)
 
 // Shared-memory layout.  Regions are 16-byte aligned; the FP32 factor goes
 // last and is placed in shared memory only if the whole layout fits.
-SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem)
+SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem)
 {
     SmemLayout L;
     int off = 0;
@@ -95,9 +103,17 @@ SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int max_smem, i
     L.rhs = f64 ? -1 : take(8 * (size_t)Kpmax);
     L.z = f64 ? -1 : take(4 * (size_t)Kpmax);
     L.red = f64 ? -1 : take(4 * (NT / 32));
+    const bool pcg = !f64 && inner == INNER_PCG;
+    L.cgx = pcg ? take(4 * (size_t)Kpmax) : -1;
+    L.cgr = pcg ? take(4 * (size_t)Kpmax) : -1;
+    L.cgp = pcg ? take(4 * (size_t)Kpmax) : -1;
+    L.cgq = pcg ? take(4 * (size_t)Kpmax) : -1;
+    L.cgpl = pcg ? take(4 * (size_t)Kpmax) : -1;
+    L.cgdinv = pcg ? take(4 * (size_t)Kpmax) : -1;
+    L.cgred = pcg ? take(4 * 2 * (NT / 32)) : -1;
     L.fac = -1;
     *fac_in_smem = 0;
-    if (!f64) {
+    if (!f64 && !pcg) {
         size_t fb = 4 * (size_t)bp_elems(Kpmax / TILE, MIX_LDB);
         if (off + fb <= (size_t)max_smem) {
             L.fac = take(fb);
@@ -121,7 +137,7 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
         return step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
     }
     BPack<float, MIX_LDB> A{cv.fac};
-    return step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s, cv.ms, a.prec == 2);
+    return step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s, cv.ms, cv.cg, a.prec == 2, a.inner);
 }
 
 __device__ __forceinline__ void check_finite(const PathArgs& a, const double* v, int K, int ii, int where,

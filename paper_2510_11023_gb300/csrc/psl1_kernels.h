@@ -17,6 +17,7 @@ struct TableJob {
 struct SmemLayout {
     int cur, hist, nxt, F, v, wp, wm, fp, fm, g, bad;     // FP64 path (+ common)
     int cdf, wpd, wmd, fpd, fmd, gdf, ydf, x, rhs, z, red, fac;   // FP32-pipe path
+    int cgx, cgr, cgp, cgq, cgpl, cgdinv, cgred;                 // PCG inner solver
     int total;
 };
 
@@ -36,9 +37,10 @@ struct PathArgs {
     int prec;                // PSL1_PREC_*
     SmemLayout L;            // shared-memory layout of the step kernels
     int fac_in_smem;         // FP32 factor in shared memory (else in the work slot)
+    int inner;               // INNER_CHOL or INNER_PCG (FP32-pipe paths)
 };
 
-SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem);
+SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem);
 
 size_t step_smem_bytes(const PathArgs& a);
 

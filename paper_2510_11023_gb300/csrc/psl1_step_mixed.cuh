@@ -144,6 +144,287 @@ __device__ void fill_matrix32(const InstDev& I, const df* g, double mu, BPack<fl
     __syncthreads();
 }
 
+// ------------------------------------------------------------------ FP32 factor with inverted diagonal blocks
+// Right-looking blocked Cholesky whose diagonal blocks end up holding
+// inv(L_JJ) instead of L_JJ: the panel solve becomes a row-parallel product
+// and each diagonal triangular solve a 32-wide matrix-vector product, so only
+// the 32-column factorisation of a diagonal block is sequential.
+
+// Warp-cooperative: factor the 32x32 block D (row stride MIX_LDB) and
+// overwrite it with inv(L).  Lane i holds row i in registers.
+__device__ __forceinline__ void diag_factor_inv32(float* D, int J, int* bad)
+{
+    const int lane = threadIdx.x & 31;
+    float a[TILE];
+#pragma unroll
+    for (int p = 0; p < TILE; ++p) a[p] = p <= lane ? D[lane * MIX_LDB + p] : 0.f;
+#pragma unroll
+    for (int j = 0; j < TILE; ++j) {
+        float piv = __shfl_sync(0xffffffffu, a[j], j);
+        if (!(piv > 0.f)) {
+            if (lane == 0 && *bad < 0) *bad = TILE * J + j;
+            piv = 1.f;
+        }
+        float d = sqrtf(piv), rd = 1.0f / d;
+        if (lane == j) a[j] = d;
+        if (lane > j) a[j] *= rd;
+#pragma unroll
+        for (int k = j + 1; k < TILE; ++k) {
+            float lkj = __shfl_sync(0xffffffffu, a[j], k);
+            if (lane >= k) a[k] -= a[j] * lkj;
+        }
+    }
+    // L to shared memory, then lane c computes column c of inv(L) by forward substitution
+#pragma unroll
+    for (int p = 0; p < TILE; ++p)
+        if (p <= lane) D[lane * MIX_LDB + p] = a[p];
+    __syncwarp();
+    float x[TILE];
+#pragma unroll
+    for (int i = 0; i < TILE; ++i) {
+        float s = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+        for (int p = 0; p < i; ++p) s -= D[i * MIX_LDB + p] * x[p];
+        x[i] = (i >= lane) ? s / D[i * MIX_LDB + i] : 0.f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < TILE; ++i)
+        if (i >= lane) D[i * MIX_LDB + lane] = x[i];
+    __syncwarp();
+}
+
+__device__ void chol32_factor_inv(BPack<float, MIX_LDB> A, int nb, int* bad)
+{
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int J = 0; J < nb; ++J) {
+        if (warp == 0) diag_factor_inv32(A.blk(J, J), J, bad);
+        __syncthreads();
+        // panel: L_IJ = A_IJ inv(L_JJ)^T, one row per thread, in place
+        const float* Li = A.blk(J, J);
+        const int nrows = (nb - J - 1) * TILE;
+        for (int rr = tid; rr < nrows; rr += NT) {
+            float* row = A.blk(J + 1 + rr / TILE, J) + (rr % TILE) * MIX_LDB;
+            float in[TILE], out[TILE];
+#pragma unroll
+            for (int p = 0; p < TILE; ++p) {
+                in[p] = row[p];
+                out[p] = 0.f;
+            }
+#pragma unroll
+            for (int c = 0; c < TILE; ++c)
+#pragma unroll
+                for (int p = 0; p <= c; ++p) out[c] += in[p] * Li[c * MIX_LDB + p];
+#pragma unroll
+            for (int p = 0; p < TILE; ++p) row[p] = out[p];
+        }
+        __syncthreads();
+        const int nrem = nb - J - 1;
+        const int ntiles = nrem * (nrem + 1) / 2 * 64;
+        for (int t = tid; t < ntiles; t += NT) {
+            int pr = t >> 6, tt = t & 63;
+            int a = (int)((sqrtf(8.0f * pr + 1.0f) - 1.0f) * 0.5f);
+            while ((a + 1) * (a + 2) / 2 <= pr) ++a;
+            while (a * (a + 1) / 2 > pr) --a;
+            int b = pr - a * (a + 1) / 2;
+            int I = J + 1 + a, I2 = J + 1 + b;
+            int ti = tt >> 3, tj = tt & 7;
+            if (I == I2 && tj > ti) continue;
+            const float* La = A.blk(I, J) + (4 * ti) * MIX_LDB;
+            const float* Lb = A.blk(I2, J) + (4 * tj) * MIX_LDB;
+            float acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+#pragma unroll 8
+            for (int p = 0; p < TILE; ++p) {
+                float x[4], y[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    x[r] = La[r * MIX_LDB + p];
+                    y[r] = Lb[r * MIX_LDB + p];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(x[r], y[c], acc[r][c]);
+            }
+            float* C = A.blk(I, I2) + (4 * ti) * MIX_LDB + 4 * tj;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) C[r * MIX_LDB + c] -= acc[r][c];
+        }
+        __syncthreads();
+    }
+}
+
+// Solve L L^T x = v in place with the factor of chol32_factor_inv.  Every warp
+// forms the 32 diagonal-block results itself (a 32-term product per lane), so
+// one barrier per block suffices; the block's results are stored one block later.
+__device__ void chol32_solve_inv(BPack<float, MIX_LDB> A, int nb, float* v)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float ylast = 0.f;
+    for (int J = 0; J < nb; ++J) {
+        const float* Li = A.blk(J, J);
+        float y = 0.f;
+#pragma unroll
+        for (int p = 0; p < TILE; ++p)
+            if (p <= lane) y += Li[lane * MIX_LDB + p] * v[TILE * J + p];
+        if (J > 0 && warp == 0) v[TILE * (J - 1) + lane] = ylast;
+        ylast = y;
+        const int nrows = (nb - J - 1) * TILE;
+        for (int rb = warp * 32; rb < nrows; rb += NT) {   // warp-uniform row blocks
+            int rr = rb + lane;
+            float s = 0.f;
+            const float* row = A.blk(J + 1 + rr / TILE, J) + (rr % TILE) * MIX_LDB;
+#pragma unroll
+            for (int p = 0; p < TILE; ++p) s += row[p] * __shfl_sync(0xffffffffu, y, p);
+            v[TILE * (J + 1) + rr] -= s;
+        }
+        __syncthreads();
+    }
+    if (warp == 0) v[TILE * (nb - 1) + lane] = ylast;
+    __syncthreads();
+    float xlast = 0.f;
+    for (int J = nb - 1; J >= 0; --J) {
+        const float* Li = A.blk(J, J);
+        float x = 0.f;
+#pragma unroll
+        for (int p = 0; p < TILE; ++p)
+            if (p >= lane) x += Li[p * MIX_LDB + lane] * v[TILE * J + p];
+        if (J < nb - 1 && warp == 0) v[TILE * (J + 1) + lane] = xlast;
+        xlast = x;
+        const int ncols = J * TILE;
+        for (int cb = warp * 32; cb < ncols; cb += NT) {
+            int cc = cb + lane;
+            const float* blk = A.blk(J, cc / TILE);
+            int c = cc % TILE;
+            float s = 0.f;
+#pragma unroll
+            for (int r = 0; r < TILE; ++r) s += blk[r * MIX_LDB + c] * __shfl_sync(0xffffffffu, x, r);
+            v[cc] -= s;
+        }
+        __syncthreads();
+    }
+    if (warp == 0) v[lane] = xlast;
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ FP32 PCG inner solver
+// z = M^{-1} r approximately, M = I + mu cA k l (g_|k-l| + g_{k+l}) applied in
+// FP32 from the moments' hi parts, Jacobi preconditioner.  For
+// 0 < D_- <= D <= D_+ (the paper's Eq. Assumptions) the Jacobi-scaled operator
+// has condition number about D_+/D_-, so a few iterations reduce the residual
+// by FP32's resolution.  r: ms.z on entry; result in ms.z.
+constexpr int PCG_MAXIT = 40;
+constexpr float PCG_RTOL = 1e-6f;
+
+struct PcgSmem {
+    float *x, *r, *p, *q, *pl, *dinv;   // Kp each
+    float* red2;                         // 2 * NT/32
+};
+
+__device__ __forceinline__ float2 block_sum2(float a, float b, float* red2)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        red2[threadIdx.x >> 5] = a;
+        red2[NT / 32 + (threadIdx.x >> 5)] = b;
+    }
+    __syncthreads();
+    float sa = 0.f, sb = 0.f;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        sa += red2[w];
+        sb += red2[NT / 32 + w];
+    }
+    return make_float2(sa, sb);
+}
+
+__device__ void pcg32(const InstDev& I, double mu, MixSmem& ms, PcgSmem& cg, int maxit, float rtol)
+{
+    const int K = I.K, tid = threadIdx.x;
+    const float sc = (float)(mu * I.cA);
+    const df* g = ms.gdf;
+    // normalise the right-hand side (refinement residuals can be ~1e-15 of the
+    // solution; unscaled, the FP32 inner products would underflow)
+    float rmax = 0.f;
+    for (int k = tid; k < K; k += NT) rmax = fmaxf(rmax, fabsf(ms.z[k]));
+    rmax = block_max(rmax, ms.red);
+    if (!(rmax > 0.f) || !isfinite(rmax)) {
+        __syncthreads();
+        for (int k = tid; k < I.Kp; k += NT) ms.z[k] = 0.f;
+        __syncthreads();
+        return;
+    }
+    const float rs = 1.0f / rmax;
+    float rz = 0.f, rr = 0.f;
+    for (int k = tid; k < K; k += NT) {
+        float d = 1.0f + sc * (float)((k + 1) * (k + 1)) * (g[0].hi + g[2 * k + 2].hi);
+        float di = 1.0f / d;
+        float r = ms.z[k] * rs, z = di * r;
+        cg.dinv[k] = di;
+        cg.x[k] = 0.f;
+        cg.r[k] = r;
+        cg.p[k] = z;
+        cg.pl[k] = (float)(k + 1) * z;
+        rz += r * z;
+        rr += r * r;
+    }
+    float2 s0 = block_sum2(rz, rr, cg.red2);
+    rz = s0.x;
+    const float stop = rtol * rtol * s0.y;
+    for (int it = 0; it < maxit && s0.y > 0.f; ++it) {
+        // q = M p, and p.q
+        float pq = 0.f;
+        for (int k = tid; k < K; k += NT) {
+            float acc = 0.f;
+            for (int l = 0; l < K; ++l) {
+                int d = k > l ? k - l : l - k;
+                acc = fmaf(g[d].hi + g[k + l + 2].hi, cg.pl[l], acc);
+            }
+            float q = cg.p[k] + sc * (float)(k + 1) * acc;
+            cg.q[k] = q;
+            pq += cg.p[k] * q;
+        }
+        float2 s1 = block_sum2(pq, 0.f, cg.red2);
+        if (!(s1.x > 0.f)) {   // M p . p <= 0: not SPD (D <= 0 somewhere)
+            if (tid == 0 && *ms.flag < 0) *ms.flag = 0;
+            break;
+        }
+        float alpha = rz / s1.x;
+        float rzn = 0.f, rrn = 0.f;
+        for (int k = tid; k < K; k += NT) {
+            cg.x[k] = fmaf(alpha, cg.p[k], cg.x[k]);
+            float r = fmaf(-alpha, cg.q[k], cg.r[k]);
+            cg.r[k] = r;
+            float z = cg.dinv[k] * r;
+            cg.q[k] = z;                      // q holds z until the p update
+            rzn += r * z;
+            rrn += r * r;
+        }
+        float2 s2 = block_sum2(rzn, rrn, cg.red2);
+        if (s2.y <= stop) break;
+        float beta = rz > 0.f ? s2.x / rz : 0.f;
+        rz = s2.x;
+        for (int k = tid; k < K; k += NT) {
+            float p = fmaf(beta, cg.p[k], cg.q[k]);
+            cg.p[k] = p;
+            cg.pl[k] = (float)(k + 1) * p;
+        }
+        __syncthreads();
+    }
+    for (int k = tid; k < I.Kp; k += NT) ms.z[k] = k < K ? cg.x[k] * rmax : 0.f;
+    __syncthreads();
+}
+
 // r = rhs - (I + mu cA k l T+H(g)) x, matrix applied in double-float.
 __device__ void residual_df(const InstDev& I, double mu, MixSmem& ms)
 {
@@ -168,11 +449,13 @@ __device__ void residual_df(const InstDev& I, double mu, MixSmem& ms)
 // The step: c (K, shared) -> out (K, shared).  Returns the first bad pivot or -1.
 __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, const double* c,
                           const double* hist, double te, double mu, double* out, double* F,
-                          BPack<float, MIX_LDB> A, StepSmem& s, MixSmem& ms, bool fp32_only)
+                          BPack<float, MIX_LDB> A, StepSmem& s, MixSmem& ms, PcgSmem& cg, bool fp32_only,
+                          int inner)
 {
     const int tid = threadIdx.x;
     nodes_moments_mixed(I, Tb, tp, c, te, ms, F, fp32_only);
-    fill_matrix32(I, ms.gdf, mu, A);
+    if (inner == INNER_CHOL) fill_matrix32(I, ms.gdf, mu, A);
+    // refinement from x = 0: the first correction is the FP32 solve of rhs
     for (int k = tid; k < I.Kp; k += NT) {
         double r = k < I.K ? hist[k] + mu * F[k] : 0.0;
         ms.rhs[k] = r;
@@ -181,8 +464,12 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
     }
     if (tid == 0) *s.bad = -1;
     __syncthreads();
-    chol_factor<float, MIX_LDB>(A, I.nb, s.bad);
-    chol_solve<float, MIX_LDB, float>(A, I.nb, ms.z);
+    if (inner == INNER_CHOL) {
+        chol32_factor_inv(A, I.nb, s.bad);
+        chol32_solve_inv(A, I.nb, ms.z);
+    } else {
+        pcg32(I, mu, ms, cg, PCG_MAXIT, PCG_RTOL);
+    }
     for (int sweep = 0;; ++sweep) {
         float zmax = 0.f, xmax = 0.f;
         for (int k = tid; k < I.K; k += NT) {
@@ -194,9 +481,12 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
         zmax = block_max(zmax, ms.red);
         __syncthreads();
         xmax = block_max(xmax, ms.red);
-        if (fp32_only || zmax <= 1e-11f * xmax || sweep >= 6) break;
+        if (fp32_only || zmax <= 1e-11f * xmax || sweep >= 6 || *s.bad >= 0) break;
         residual_df(I, mu, ms);
-        chol_solve<float, MIX_LDB, float>(A, I.nb, ms.z);
+        if (inner == INNER_CHOL)
+            chol32_solve_inv(A, I.nb, ms.z);
+        else
+            pcg32(I, mu, ms, cg, PCG_MAXIT, PCG_RTOL);
     }
     for (int k = tid; k < I.K; k += NT) out[k] = ms.x[k];
     __syncthreads();
