@@ -140,26 +140,6 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- work accounting
-def step_flops(K: int, hist_terms: int) -> float:
-    """Algorithmic FLOPs of one linearised fine step with K modes, Q = 2K nodes:
-    mirror-folded transforms u (K^2), moments (2K^2), load (K^2) MACs; Cholesky
-    K^3/6 MACs; two triangular solves K^2 MACs; history hist_terms*K MACs."""
-    macs = K**3 / 6.0 + 4.0 * K * K + K * K + hist_terms * K
-    return 2.0 * macs
-
-
-def fstage_flops(wl, iters) -> float:
-    """FLOPs of all F-stage launches of one parareal solve (slices n >= k at iteration k)."""
-    tot = 0.0
-    for b, s in enumerate(wl.specs):
-        K, m = s.K, s.nsteps // wl.P
-        per_r = sum(r - 1 for r in range(1, m + 1))
-        for k in range(int(iters[b])):
-            for n in range(k, wl.P):
-                tot += m * step_flops(K, 0) + 2.0 * K * (per_r + m * n)
-    return tot
-
-
 def rel_err(U, S) -> float:
     """max over instances of max_n ||U_n - S_n||_2 / max_n ||S_n||_2."""
     return max(float(np.sqrt(((u - s) ** 2).sum(1)).max() / np.sqrt((s**2).sum(1)).max()) for u, s in zip(U, S))
@@ -278,7 +258,7 @@ def main():
     torch.cuda.synchronize()
     clk = ClockSampler(dist.local)
     clk.start()
-    times, fine_ms, fine_launches, flops, launches, iters_all = [], 0.0, 0, 0.0, 0, []
+    times, fine_ms, coarse_ms, fine_launches, flops, launches, iters_all = [], 0.0, 0.0, 0, 0.0, 0, []
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1.0)
@@ -292,9 +272,10 @@ def main():
         its = pr.get_iterations()
         iters_all.append(int(its.max()))
         fine_ms += st["ms_fine"]
+        coarse_ms += st["ms_coarse"]
         fine_launches += st["iterations_max"]
         launches += st["kernel_launches"]
-        flops += fstage_flops(wl, its)
+        flops += st["flop_fine"]
     torch.cuda.synchronize()
     dist.barrier()
     wall = time.perf_counter() - t_wall0
@@ -328,6 +309,9 @@ def main():
     peak = fp64_tf if args.precision == "fp64" else fp32_tf
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "kernel": "k_fstage",
+            "share_of_solve": {"k_fstage": fine_ms / max(sum(times), 1e-9),
+                               "k_coarse_sweep": coarse_ms / max(sum(times), 1e-9)},
+            "flops_source": "algorithmic FLOPs counted per step on the device (psl1_stats.flop_fine)",
             "peak_source": ("measured FP64 FMA throughput (psl1_probe_peaks)" if args.precision == "fp64"
                             else "measured FP32 FMA throughput (psl1_probe_peaks)")}
 

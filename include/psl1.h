@@ -105,6 +105,9 @@ typedef struct {
     double ms_history;       /* device time in history kernels                  */
     double fine_steps;       /* linearised fine steps executed (all instances)  */
     double fine_step_modes;  /* sum over executed fine steps of K               */
+    double flop_fine;        /* algorithmic FLOPs done in fine-propagator launches */
+    double flop_coarse;      /* algorithmic FLOPs done in coarse sweeps          */
+    double flop_serial;      /* algorithmic FLOPs done by the serial solvers     */
 } psl1_stats;
 
 /* Create a batch of `batch` instances sharing the slice count P (every

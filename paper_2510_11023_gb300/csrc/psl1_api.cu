@@ -50,6 +50,7 @@ struct psl1_problem {
     int2* d_units = nullptr;
     int nunits = 0;
     DevStatus* d_status = nullptr;
+    double* d_flops = nullptr;   // algorithmic FLOP accumulators: F stage, coarse, serial, pieces
     // uniform solver pools (lazy)
     double *d_Wcur = nullptr, *d_dW = nullptr, *d_part = nullptr;
     int uni_chunk = 256, uni_maxchunks = 0;
@@ -125,6 +126,19 @@ static psl1_status check_device_status(psl1_problem* h)
 static psl1_status reset_status(psl1_problem* h)
 {
     CU(h, cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream));
+    if (h->d_flops) CU(h, cudaMemsetAsync(h->d_flops, 0, 4 * sizeof(double), h->stream));
+    return PSL1_OK;
+}
+
+// Copy the device FLOP accumulators into the statistics (after a synchronising call).
+static psl1_status read_flops(psl1_problem* h)
+{
+    double f[4] = {0, 0, 0, 0};
+    CU(h, cudaMemcpyAsync(f, h->d_flops, sizeof f, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    h->stats.flop_fine = f[0];
+    h->stats.flop_coarse = f[1];
+    h->stats.flop_serial = f[2];
     return PSL1_OK;
 }
 
@@ -326,6 +340,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     CTRY(dalloc(h, &h->d_active, batch));
     CTRY(dalloc(h, &h->d_counter, 1));
     CTRY(dalloc(h, &h->d_status, 1));
+    CTRY(dalloc(h, &h->d_flops, 4));
     // per-slot factor workspace: FP64 factor, or the FP32 factor when it does not fit in shared memory
     long long work_stride = precision == PSL1_PREC_FP64 ? bp_elems(nbmax, TILE)
                             : (fac_in_smem || inner == INNER_PCG) ? 1
@@ -394,6 +409,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.L = lay;
     a.fac_in_smem = fac_in_smem;
     a.inner = inner;
+    a.flops = h->d_flops;
+    a.flop_slot = 3;
     h->iters.assign(batch, 0);
     h->errlog.assign(batch, {});
     h->d_Ucur = h->d_Ua;
@@ -510,6 +527,7 @@ psl1_status psl1_solve_serial(psl1_h h, int kind)
     CU(h, cudaEventRecord(h->ev[1], h->stream));
     TRY(check_device_status(h));
     h->stats.ms_fine = elapsed(h->ev[0], h->ev[1]);
+    TRY(read_flops(h));
     h->stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     h->ser_done = true;
     return PSL1_OK;
@@ -604,6 +622,7 @@ psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_o
         bool conv = (!h->errlog[b].empty() && h->errlog[b].back() <= tol) || h->iters[b] >= P;
         if (!conv) all_conv = false;
     }
+    TRY(read_flops(h));
     h->stats.iterations_max = itmax;
     if (iters_out) *iters_out = itmax;
     h->stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -132,12 +132,32 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
                                        const double* hist, double te, double mu, double* out, Carve& cv)
 {
     const TabDev& Tb = a.tab[I.tab];
+    int bad;
+    if (threadIdx.x == 0) {
+        cv.s.bad[1] = 0;
+        cv.s.bad[2] = 0;
+    }
     if (a.prec == 0) {
         BPack<double, TILE> A{a.work + (size_t)blockIdx.x * a.work_stride};
-        return step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
+        bad = step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
+    } else {
+        BPack<float, MIX_LDB> A{cv.fac};
+        bad = step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s, cv.ms, cv.cg, a.prec == 2, a.inner);
     }
-    BPack<float, MIX_LDB> A{cv.fac};
-    return step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s, cv.ms, cv.cg, a.prec == 2, a.inner);
+    // algorithmic FLOPs of the step: transforms (u, moments, load: 4 K^2 multiply-adds with
+    // Q = 2K nodes), coefficient evaluation (~30 per node), and the solve -- FP64: Cholesky
+    // K^3/3 + two triangular solves 2 K^2; FP32 pipes: 4 K^2 per Toeplitz+Hankel product
+    // (refinement residuals and PCG iterations).
+    if (threadIdx.x == 0 && a.flops) {
+        const double K = I.K, K2 = K * K;
+        double f = 8.0 * K2 + 30.0 * I.Q;
+        if (a.prec == 0)
+            f += K * K2 / 3.0 + 2.0 * K2;
+        else
+            f += 4.0 * K2 * (cv.s.bad[1] + cv.s.bad[2]) + (a.inner == INNER_CHOL ? K * K2 / 3.0 : 0.0);
+        atomicAdd(a.flops + a.flop_slot, f);
+    }
+    return bad;
 }
 
 __device__ __forceinline__ void check_finite(const PathArgs& a, const double* v, int K, int ii, int where,
@@ -171,6 +191,7 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
                 h -= bc[(size_t)(n - i) * m] * (U[(size_t)i * K + k] - U[(size_t)(i - 1) * K + k]);
             cv.hist[k] = h;
         }
+        if (tid == 0 && a.flops) atomicAdd(a.flops + a.flop_slot, 2.0 * K * (r - 1 + n));
         __syncthreads();
         int bad = do_step(a, I, cv.cur, cv.hist, I.dT * n + I.dt * (r - 1), I.mu, cv.nxt, cv);
         if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_FINE, n * m + r);
@@ -199,6 +220,7 @@ __device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, C
         cv.cur[k] = c;
         cv.hist[k] = h;
     }
+    if (tid == 0 && a.flops) atomicAdd(a.flops + a.flop_slot, 2.0 * K * n);
     __syncthreads();
     int bad = do_step(a, I, cv.cur, cv.hist, I.dT * n, I.muT, cv.nxt, cv);
     if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_COARSE, n);
@@ -407,6 +429,13 @@ __global__ void __launch_bounds__(NT) k_one_coarse(PathArgs a, int ii, int n, co
     for (int k = threadIdx.x; k < I.K; k += NT) out[k] = cv.nxt[k];
 }
 
+static PathArgs slot(const PathArgs& a, int s)
+{
+    PathArgs b = a;
+    b.flop_slot = s;
+    return b;
+}
+
 // ------------------------------------------------------------------ allocation-free slice
 // For callers that must not allocate device memory while they run (a real-time
 // loop whose memory was planned up front, or code running under an allocator
@@ -471,7 +500,7 @@ cudaError_t launch_fstage(const PathArgs& a, const double* Uold, double* Fv, con
     cudaError_t e = prep(k_fstage, sm);
     if (e != cudaSuccess) return e;
     if (grid > a.nslots) grid = a.nslots;
-    k_fstage<<<grid, NT, sm, s>>>(a, Uold, Fv, units, nunits, counter, nfirst, active);
+    k_fstage<<<grid, NT, sm, s>>>(slot(a, 0), Uold, Fv, units, nunits, counter, nfirst, active);
     return cudaGetLastError();
 }
 
@@ -482,7 +511,7 @@ cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, cons
     size_t sm = step_smem_bytes(a);
     cudaError_t e = prep(k_coarse_sweep, sm);
     if (e != cudaSuccess) return e;
-    k_coarse_sweep<<<B, NT, sm, s>>>(a, u0, Uold, Unew, Fv, Gold, init, nfirst, active, incr);
+    k_coarse_sweep<<<B, NT, sm, s>>>(slot(a, 1), u0, Uold, Unew, Fv, Gold, init, nfirst, active, incr);
     return cudaGetLastError();
 }
 
@@ -491,7 +520,7 @@ cudaError_t launch_serial_hyb(const PathArgs& a, int B, const double* u0, double
     size_t sm = step_smem_bytes(a);
     cudaError_t e = prep(k_serial_hyb, sm);
     if (e != cudaSuccess) return e;
-    k_serial_hyb<<<B, NT, sm, s>>>(a, u0, Us);
+    k_serial_hyb<<<B, NT, sm, s>>>(slot(a, 2), u0, Us);
     return cudaGetLastError();
 }
 
@@ -517,7 +546,7 @@ cudaError_t launch_uni_step(const PathArgs& a, int B, double* Wcur, double* dW, 
     size_t sm = step_smem_bytes(a);
     cudaError_t e = prep(k_uni_step, sm);
     if (e != cudaSuccess) return e;
-    k_uni_step<<<B, NT, sm, s>>>(a, Wcur, dW, Us, j, part, chunk, maxchunks);
+    k_uni_step<<<B, NT, sm, s>>>(slot(a, 2), Wcur, dW, Us, j, part, chunk, maxchunks);
     return cudaGetLastError();
 }
 
@@ -527,7 +556,7 @@ cudaError_t launch_one_step(const PathArgs& a, int b, const double* c, const dou
     size_t sm = step_smem_bytes(a);
     cudaError_t e = prep(k_one_step, sm);
     if (e != cudaSuccess) return e;
-    k_one_step<<<1, NT, sm, s>>>(a, b, c, hist, te, mu, out);
+    k_one_step<<<1, NT, sm, s>>>(slot(a, 3), b, c, hist, te, mu, out);
     return cudaGetLastError();
 }
 
@@ -536,7 +565,7 @@ cudaError_t launch_one_slice(const PathArgs& a, int b, int n, const double* U, d
     size_t sm = step_smem_bytes(a);
     cudaError_t e = prep(k_one_slice, sm);
     if (e != cudaSuccess) return e;
-    k_one_slice<<<1, NT, sm, s>>>(a, b, n, U, V);
+    k_one_slice<<<1, NT, sm, s>>>(slot(a, 3), b, n, U, V);
     return cudaGetLastError();
 }
 
@@ -545,7 +574,7 @@ cudaError_t launch_one_coarse(const PathArgs& a, int b, int n, const double* U, 
     size_t sm = step_smem_bytes(a);
     cudaError_t e = prep(k_one_coarse, sm);
     if (e != cudaSuccess) return e;
-    k_one_coarse<<<1, NT, sm, s>>>(a, b, n, U, out);
+    k_one_coarse<<<1, NT, sm, s>>>(slot(a, 3), b, n, U, out);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,8 @@ struct PathArgs {
     SmemLayout L;            // shared-memory layout of the step kernels
     int fac_in_smem;         // FP32 factor in shared memory (else in the work slot)
     int inner;               // INNER_CHOL or INNER_PCG (FP32-pipe paths)
+    double* flops;           // algorithmic FLOP accumulators (by slot), may be null
+    int flop_slot;           // 0 F stage, 1 coarse sweeps, 2 serial solvers, 3 single pieces
 };
 
 SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem);

@@ -37,7 +37,7 @@ struct MixSmem {
     double* rhs;  // Kp
     float* z;     // Kp  FP32 correction
     float* red;   // NT/32 reduction scratch
-    int* flag;
+    int* flag;    // [0] first bad pivot, [1] PCG iterations, [2] refinement residuals of the step
 };
 
 __device__ __forceinline__ float block_max(float v, float* red)
@@ -382,6 +382,7 @@ __device__ void pcg32(const InstDev& I, double mu, MixSmem& ms, PcgSmem& cg, int
     rz = s0.x;
     const float stop = rtol * rtol * s0.y;
     for (int it = 0; it < maxit && s0.y > 0.f; ++it) {
+        if (tid == 0) ms.flag[1] += 1;
         // q = M p, and p.q
         float pq = 0.f;
         for (int k = tid; k < K; k += NT) {
@@ -482,6 +483,7 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
         __syncthreads();
         xmax = block_max(xmax, ms.red);
         if (fp32_only || zmax <= 1e-11f * xmax || sweep >= 6 || *s.bad >= 0) break;
+        if (tid == 0) ms.flag[2] += 1;
         residual_df(I, mu, ms);
         if (inner == INNER_CHOL)
             chol32_solve_inv(A, I.nb, ms.z);

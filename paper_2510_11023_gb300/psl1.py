@@ -43,7 +43,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("iterations_max", ctypes.c_int), ("kernel_launches", ctypes.c_int),
                 ("ms_total", ctypes.c_double), ("ms_fine", ctypes.c_double), ("ms_coarse", ctypes.c_double),
                 ("ms_history", ctypes.c_double), ("fine_steps", ctypes.c_double),
-                ("fine_step_modes", ctypes.c_double)]
+                ("fine_step_modes", ctypes.c_double), ("flop_fine", ctypes.c_double),
+                ("flop_coarse", ctypes.c_double), ("flop_serial", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
