@@ -197,6 +197,63 @@ psl1_status psl1_fine_slice_noalloc(psl1_h h, int b, int n, const double* d_U, d
 /* Coarse propagator G_n of instance b on U_0..U_n (host); out: K_b doubles. */
 psl1_status psl1_coarse_step(psl1_h h, int b, int n, const double* U, double* out);
 
+/* ---- learned coarse correction (no counterpart in the paper) ------------
+ * A reading of the learned coarse propagator: it corrects the L1 coarse
+ * propagator rather than replacing it,
+ *   G_theta(U_{0:n}) = G_n(U_{0:n}) + s o MLP(z_n),
+ *   z_n = [k^2 U_n(k), k <= nU ; k^2 eta_n(k), k <= nH ; alpha ; T_n],
+ *   eta_n = sum_{j<n} b_{n-j} (U_{j+1} - U_j)  (the coarse L1 history of Eq.
+ *   NumericalSchemeSequential), modes beyond an instance's K read as 0,
+ * MLP = Linear(nU+nH+2, W) SiLU Linear(W, W) SiLU Linear(W, W) SiLU
+ * Linear(W, nout), applied to the first nout modes; BF16 weight copies,
+ * FP32 accumulation, FP32 master weights and Adam state.  The output layer
+ * starts at zero, so an untrained network is exactly the L1 G (its fallback).
+ * Parareal converges to the sequential fine solution for ANY coarse
+ * propagator (Eq. PararealConvergence); the network only changes the
+ * number of iterations.  Flat parameter layout: W1[W][nin] b1[W] W2[W][W]
+ * b2[W] W3[W][W] b3[W] W4[nout][W] b4[nout], nin = nU+nH+2.               */
+typedef struct psl1_mlp* psl1_mlp_h;
+
+/* nU + nH + 2 <= 320, W <= 512, nout <= 512; weights U(-1/sqrt(fan_in), +)
+ * from a counter-based hash of (seed, index); output layer zero.          */
+psl1_status psl1_mlp_create(psl1_mlp_h* out, int nU, int nH, int width, int nout,
+                            unsigned long long seed, void* cuda_stream);
+psl1_status psl1_mlp_nparams(psl1_mlp_h mh, long long* nparams);
+/* FP32 master parameters (flat layout) and the nout output scales s (host). */
+psl1_status psl1_mlp_get_params(psl1_mlp_h mh, float* params, float* oscale);
+psl1_status psl1_mlp_set_params(psl1_mlp_h mh, const float* params, const float* oscale);
+/* Raw network output (without s) for B feature rows z (B x nin, host).     */
+psl1_status psl1_mlp_forward(psl1_mlp_h mh, int B, const float* z, float* y);
+/* loss = mean (MLP(z) - t)^2 and its gradient w.r.t. every parameter.       */
+psl1_status psl1_mlp_loss_grad(psl1_mlp_h mh, int B, const float* z, const float* t, float* grad,
+                               float* loss);
+/* One Adam step (b1 0.9, b2 0.999, eps 1e-8) with a caller-given gradient. */
+psl1_status psl1_mlp_adam_step(psl1_mlp_h mh, const float* grad, float lr);
+/* Build the training set from the instances of `data` (replacing any
+ * previous one); source is a bit mask:
+ *  PSL1_DATA_TRAJECTORIES: (z_n, U_{n+1} - G_n(U_{0:n})) on the sequential
+ *      fine solution (needs psl1_solve_serial(data, PSL1_SERIAL_HYBRID));
+ *  PSL1_DATA_ITERATES: runs `iters` parareal iterations on `data` with its
+ *      current coarse propagator and takes, after each F stage, the pairs
+ *      (z(U^k_{0:n}), F_n(U^k_{0:n}) - G_n(U^k_{0:n})) of every slice n >= k --
+ *      the exact correction parareal applies, on the states it visits.
+ * Targets are scaled per mode to unit RMS; s holds those RMS values.  The
+ * parareal buffers of `data` are overwritten.                              */
+enum { PSL1_DATA_TRAJECTORIES = 1, PSL1_DATA_ITERATES = 2 };
+psl1_status psl1_mlp_dataset(psl1_mlp_h mh, psl1_h data, int source, int iters);
+/* Train on the current training set (built from `data`'s trajectories if
+ * none exists): minibatches of `batch` in a per-epoch affine permutation,
+ * Adam with cosine-decayed learning rate lr.  loss_log (may be NULL)
+ * receives the mean loss of each epoch.                                    */
+psl1_status psl1_mlp_train(psl1_mlp_h mh, psl1_h data, int epochs, int batch, float lr,
+                           unsigned long long seed, float* loss_log);
+/* Use the learned correction in every coarse propagator of h (coarse sweeps,
+ * G_old, psl1_coarse_step); NULL restores the plain L1 G.  mh must outlive
+ * its use by h.                                                            */
+psl1_status psl1_set_coarse(psl1_h h, psl1_mlp_h mh);
+const char* psl1_mlp_last_error(psl1_mlp_h mh);
+void psl1_mlp_destroy(psl1_mlp_h mh);
+
 /* ---- measurement utility (no counterpart in the paper) ------------------ */
 /* Measured FP64 and FP32 FMA throughput of the current device in TFLOP/s
  * (dependent FMA chains on every SM, best of three timed launches).  Used

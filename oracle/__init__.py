@@ -90,9 +90,9 @@ def lib():
             "orc_serial_hyb": (ctypes.c_int, [pp, D_, D_, D_]),
             "orc_serial_uni": (ctypes.c_int, [pp, D_, D_]),
             "orc_coarse_sweep": (ctypes.c_int, [pp, D_, D_, D_, ctypes.c_int, ctypes.c_int,
-                                                ctypes.c_int, D_]),
+                                                ctypes.c_int, ctypes.c_int, D_]),
             "orc_parareal": (ctypes.c_int, [pp, D_, ctypes.c_double, ctypes.c_int, D_, ctypes.c_int,
-                                            ctypes.c_int, ctypes.c_int, D_, D_, D_, P_]),
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, D_, D_, D_, P_]),
             "orc_mlp_nparams": (ctypes.c_long, [ctypes.c_int] * 3),
             "orc_mlp_forward": (ctypes.c_int, [ctypes.c_int] * 3 + [D_, ctypes.c_int, D_, D_, D_]),
             "orc_mlp_backward": (ctypes.c_int, [ctypes.c_int] * 3 + [D_, ctypes.c_int, D_, D_, D_, D_]),
@@ -270,18 +270,20 @@ def serial_uni(p: Prob, u0):
 
 
 def _mlp_args(mlp):
+    """mlp: dict(params, oscale, nU, nH, width[, nout]) -- nout defaults to len(oscale)."""
     if mlp is None:
-        return None, None, 0, 0, 0, None, None
+        return None, None, 0, 0, 0, 0, None, None
     params, pp = _d(mlp["params"])
     osc, po = _d(mlp["oscale"])
-    return params, pp, int(mlp["nU"]), int(mlp["nH"]), int(mlp["width"]), osc, po
+    nout = int(mlp.get("nout", osc.shape[0]))
+    return params, pp, int(mlp["nU"]), int(mlp["nH"]), int(mlp["width"]), nout, osc, po
 
 
 def coarse_sweep(p: Prob, u0, mlp=None):
     u0, pu = _d(u0)
     U, pU = _out(p.P + 1, p.K)
     keep = _mlp_args(mlp)
-    _chk(lib().orc_coarse_sweep(ctypes.byref(p), pu, pU, keep[1], keep[2], keep[3], keep[4], keep[6]),
+    _chk(lib().orc_coarse_sweep(ctypes.byref(p), pu, pU, keep[1], keep[2], keep[3], keep[4], keep[5], keep[7]),
          "coarse_sweep")
     return U
 
@@ -296,7 +298,7 @@ def parareal(p: Prob, u0, tol: float, max_iter: int | None = None, mlp=None):
     it = ctypes.c_int(0)
     keep = _mlp_args(mlp)
     _chk(lib().orc_parareal(ctypes.byref(p), pu, float(tol), int(max_iter), keep[1], keep[2], keep[3],
-                            keep[4], keep[6], pU, pe, ctypes.byref(it)), "parareal")
+                            keep[4], keep[5], keep[7], pU, pe, ctypes.byref(it)), "parareal")
     k = it.value
     return Uall[: k + 1], err[:k], k
 

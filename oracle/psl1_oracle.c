@@ -593,18 +593,19 @@ void orc_adam_step(long n, double* param, const double* grad, double* m, double*
 }
 
 /* Features of the learned correction for coarse node n (see above).         */
+/* Reading for instances with fewer than nU (or nH) modes: the missing modes
+ * read as zero, so one network serves a batch of uneven K.                  */
 int orc_mlp_features(const orc_prob* p, int nU, int nH, int n, const double* U, double* z)
 {
     int K = p->Mx * (p->dim == 2 ? p->My : 1);
-    if (nU > K || nH > K) return -1;
     double* eta = calloc(K, sizeof(double));
     if (!eta) return -1;
     for (int j = 0; j <= n - 1; ++j) {
         double w = orc_b(p->alpha, (double)(n - j));
         for (int i = 0; i < K; ++i) eta[i] += w * (U[(size_t)(j + 1) * K + i] - U[(size_t)j * K + i]);
     }
-    for (int k = 0; k < nU; ++k) z[k] = (double)(k + 1) * (k + 1) * U[(size_t)n * K + k];
-    for (int k = 0; k < nH; ++k) z[nU + k] = (double)(k + 1) * (k + 1) * eta[k];
+    for (int k = 0; k < nU; ++k) z[k] = k < K ? (double)(k + 1) * (k + 1) * U[(size_t)n * K + k] : 0.0;
+    for (int k = 0; k < nH; ++k) z[nU + k] = k < K ? (double)(k + 1) * (k + 1) * eta[k] : 0.0;
     z[nU + nH] = p->alpha;
     z[nU + nH + 1] = p->T / p->P * n;
     free(eta);
@@ -797,12 +798,12 @@ int orc_serial_uni(const orc_prob* p, const double* u0, double* W)
 }
 
 int orc_coarse_sweep(const orc_prob* p, const double* u0, double* U, const double* mlp_params,
-                     int nU, int nH, int width, const double* oscale)
+                     int nU, int nH, int width, int nout, const double* oscale)
 {
     orc_disc d;
     if (disc_build(p, &d)) return -1;
     int K = d.K, st = 0;
-    orc_mlp mm = {nU, nH, width, K, mlp_params, oscale};
+    orc_mlp mm = {nU, nH, width, nout, mlp_params, oscale};
     memcpy(U, u0, sizeof(double) * K);
     for (int n = 0; n < p->P && st == 0; ++n)
         st = coarse_step(p, &d, n, U, mlp_params ? &mm : NULL, U + (size_t)(n + 1) * K);
@@ -827,14 +828,14 @@ int orc_coarse_sweep(const orc_prob* p, const double* u0, double* U, const doubl
 /* is not NULL (the same G at both call sites of the iteration).             */
 /* ------------------------------------------------------------------------ */
 int orc_parareal(const orc_prob* p, const double* u0, double tol, int max_iter,
-                 const double* mlp_params, int nU, int nH, int width, const double* oscale,
+                 const double* mlp_params, int nU, int nH, int width, int nout, const double* oscale,
                  double* Uall, double* errlog, int* iters_out)
 {
     orc_disc d;
     if (disc_build(p, &d)) return -1;
     int K = d.K, P = p->P, m = p->N / p->P, st = 0;
     size_t slab = (size_t)(P + 1) * K;
-    orc_mlp mm = {nU, nH, width, K, mlp_params, oscale};
+    orc_mlp mm = {nU, nH, width, nout, mlp_params, oscale};
     const orc_mlp* mp = mlp_params ? &mm : NULL;
     double* Gold = malloc(sizeof(double) * (size_t)P * K);
     double* Fold = malloc(sizeof(double) * (size_t)P * K);

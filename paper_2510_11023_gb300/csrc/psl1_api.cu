@@ -57,6 +57,7 @@ struct psl1_problem {
     PathArgs pa{};
     // state
     bool u0_set = false, par_done = false, ser_done = false;
+    int ser_kind = -1;           // kind of the last serial solve
     double* d_Ucur = nullptr;   // buffer holding the current parareal iterate
     std::vector<int> iters;
     std::vector<std::vector<double>> errlog;
@@ -495,6 +496,7 @@ psl1_status psl1_solve_serial(psl1_h h, int kind)
     h->stats = psl1_stats{};
     TRY(reset_status(h));
     CU(h, cudaEventRecord(h->ev[0], h->stream));
+    h->ser_kind = kind;
     if (kind == PSL1_SERIAL_HYBRID) {
         CU(h, launch_serial_hyb(h->pa, h->B, h->d_u0, h->d_Us, h->stream));
         h->stats.kernel_launches = 1;
@@ -761,6 +763,363 @@ psl1_status psl1_coarse_step(psl1_h h, int b, int n, const double* U, double* ou
     CU(h, launch_one_coarse(h->pa, b, n, dU, dout, h->stream));
     CU(h, cudaMemcpyAsync(out, dout, sizeof(double) * I.K, cudaMemcpyDeviceToHost, h->stream));
     return check_device_status(h);
+}
+
+// ---------------------------------------------------------------- learned coarse correction
+}  // extern "C"
+
+struct psl1_mlp {
+    MlpLayout L{};
+    int nU = 0, nH = 0, nin = 0, width = 0, nout = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void*> allocs;
+    float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *oscale = nullptr, *loss = nullptr;
+    __nv_bfloat16 *w16 = nullptr, *wT = nullptr;
+    int adam_t = 0;
+    int bcap = 0;
+    float *X0 = nullptr, *T = nullptr, *Y = nullptr, *dY = nullptr, *dH = nullptr, *dH2 = nullptr;
+    float *pre[3] = {nullptr, nullptr, nullptr}, *act[3] = {nullptr, nullptr, nullptr};
+    int S = 0;                 // sample slots in Z / R
+    int Scap = 0;
+    float *Z = nullptr, *R = nullptr;
+    int* valid = nullptr;      // indices of the slots holding samples
+    int nvalid = 0;
+    std::string err;
+
+    MlpDev dev() const
+    {
+        MlpDev d{};
+        d.wT = wT;
+        d.bias = master;
+        long long oT = 0;
+        for (int l = 0; l < 4; ++l) {
+            d.oT[l] = oT;
+            oT += (long long)L.din[l] * L.dout[l];
+            d.ob[l] = L.ob[l];
+        }
+        d.oscale = oscale;
+        d.nU = nU;
+        d.nH = nH;
+        d.nin = nin;
+        d.width = width;
+        d.nout = nout;
+        d.on = 1;
+        return d;
+    }
+};
+
+static psl1_status mfail(psl1_mlp* h, psl1_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+#define MCU(h, call)                                                                                 \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return mfail((h), PSL1_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                         __FILE__, __LINE__);                                                        \
+    } while (0)
+
+template <typename T>
+static psl1_status malloc_m(psl1_mlp* h, T** p, size_t count)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return mfail(h, PSL1_ERR_NOMEM, "cudaMalloc of %zu bytes failed", count * sizeof(T));
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return PSL1_OK;
+}
+
+static psl1_status ensure_batch(psl1_mlp* h, int B)
+{
+    if (B <= h->bcap) return PSL1_OK;
+    size_t W = h->width;
+    TRY(malloc_m(h, &h->X0, (size_t)B * h->nin));
+    TRY(malloc_m(h, &h->T, (size_t)B * h->nout));
+    TRY(malloc_m(h, &h->Y, (size_t)B * h->nout));
+    TRY(malloc_m(h, &h->dY, (size_t)B * h->nout));
+    TRY(malloc_m(h, &h->dH, (size_t)B * W));
+    TRY(malloc_m(h, &h->dH2, (size_t)B * W));
+    for (int l = 0; l < 3; ++l) {
+        TRY(malloc_m(h, &h->pre[l], (size_t)B * W));
+        TRY(malloc_m(h, &h->act[l], (size_t)B * W));
+    }
+    h->bcap = B;
+    return PSL1_OK;
+}
+
+extern "C" {
+
+const char* psl1_mlp_last_error(psl1_mlp_h h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void psl1_mlp_destroy(psl1_mlp_h h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+psl1_status psl1_mlp_create(psl1_mlp_h* out, int nU, int nH, int width, int nout, unsigned long long seed,
+                            void* stream)
+{
+    if (!out) return mfail(nullptr, PSL1_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int nin = nU + nH + 2;
+    if (nU < 1 || nH < 0 || nin > MLP_MAX_IN || width < 1 || width > MLP_MAX_WIDTH || nout < 1 || nout > MLP_MAX_OUT)
+        return mfail(nullptr, PSL1_ERR_ARG, "MLP sizes out of range (nU+nH+2 <= %d, width <= %d, nout <= %d)",
+                     MLP_MAX_IN, MLP_MAX_WIDTH, MLP_MAX_OUT);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
+        return mfail(nullptr, PSL1_ERR_CUDA, "no usable CUDA device");
+    psl1_mlp* h = new psl1_mlp();
+    h->nU = nU;
+    h->nH = nH;
+    h->nin = nin;
+    h->width = width;
+    h->nout = nout;
+    h->L = mlp_layout(nin, width, nout);
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        h->own_stream = true;
+    }
+    auto bail = [&](psl1_status st) {
+        g_create_error = h->err;
+        psl1_mlp_destroy(h);
+        return st;
+    };
+    long long n = h->L.nparam;
+    psl1_status st;
+    if ((st = malloc_m(h, &h->master, n)) || (st = malloc_m(h, &h->m, n)) || (st = malloc_m(h, &h->v, n)) ||
+        (st = malloc_m(h, &h->grad, n)) || (st = malloc_m(h, &h->oscale, nout)) || (st = malloc_m(h, &h->loss, 1)) ||
+        (st = malloc_m(h, &h->w16, n)) || (st = malloc_m(h, &h->wT, n)))
+        return bail(st);
+    std::vector<float> ones(nout, 1.0f);
+    if (cudaMemsetAsync(h->m, 0, sizeof(float) * n, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->v, 0, sizeof(float) * n, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->oscale, ones.data(), sizeof(float) * nout, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        mlp_init_params(h->master, h->L, seed, h->stream) != cudaSuccess ||
+        mlp_refresh_bf16(h->master, h->w16, h->wT, nullptr, h->L, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        h->err = "MLP initialisation failed";
+        return bail(PSL1_ERR_CUDA);
+    }
+    *out = h;
+    return PSL1_OK;
+}
+
+psl1_status psl1_mlp_nparams(psl1_mlp_h h, long long* n)
+{
+    if (!h || !n) return mfail(h, PSL1_ERR_ARG, "NULL argument");
+    *n = h->L.nparam;
+    return PSL1_OK;
+}
+
+psl1_status psl1_mlp_get_params(psl1_mlp_h h, float* params, float* oscale)
+{
+    if (!h) return mfail(h, PSL1_ERR_ARG, "NULL handle");
+    if (params) MCU(h, cudaMemcpyAsync(params, h->master, sizeof(float) * h->L.nparam, cudaMemcpyDeviceToHost, h->stream));
+    if (oscale) MCU(h, cudaMemcpyAsync(oscale, h->oscale, sizeof(float) * h->nout, cudaMemcpyDeviceToHost, h->stream));
+    MCU(h, cudaStreamSynchronize(h->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_mlp_set_params(psl1_mlp_h h, const float* params, const float* oscale)
+{
+    if (!h) return mfail(h, PSL1_ERR_ARG, "NULL handle");
+    if (params) MCU(h, cudaMemcpyAsync(h->master, params, sizeof(float) * h->L.nparam, cudaMemcpyHostToDevice, h->stream));
+    if (oscale) MCU(h, cudaMemcpyAsync(h->oscale, oscale, sizeof(float) * h->nout, cudaMemcpyHostToDevice, h->stream));
+    MCU(h, mlp_refresh_bf16(h->master, h->w16, h->wT, nullptr, h->L, h->stream));
+    MCU(h, cudaStreamSynchronize(h->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_mlp_forward(psl1_mlp_h h, int B, const float* z, float* y)
+{
+    if (!h || !z || !y || B < 1) return mfail(h, PSL1_ERR_ARG, "bad argument");
+    TRY(ensure_batch(h, B));
+    MCU(h, cudaMemcpyAsync(h->X0, z, sizeof(float) * B * h->nin, cudaMemcpyHostToDevice, h->stream));
+    MCU(h, mlp_forward(h->X0, B, h->w16, h->master, h->L, h->pre, h->act, h->Y, h->stream));
+    MCU(h, cudaMemcpyAsync(y, h->Y, sizeof(float) * B * h->nout, cudaMemcpyDeviceToHost, h->stream));
+    MCU(h, cudaStreamSynchronize(h->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_mlp_loss_grad(psl1_mlp_h h, int B, const float* z, const float* t, float* grad, float* loss)
+{
+    if (!h || !z || !t || B < 1) return mfail(h, PSL1_ERR_ARG, "bad argument");
+    TRY(ensure_batch(h, B));
+    MCU(h, cudaMemcpyAsync(h->X0, z, sizeof(float) * B * h->nin, cudaMemcpyHostToDevice, h->stream));
+    MCU(h, cudaMemcpyAsync(h->T, t, sizeof(float) * B * h->nout, cudaMemcpyHostToDevice, h->stream));
+    MCU(h, cudaMemsetAsync(h->loss, 0, sizeof(float), h->stream));
+    MCU(h, mlp_forward(h->X0, B, h->w16, h->master, h->L, h->pre, h->act, h->Y, h->stream));
+    MCU(h, mlp_backward(h->X0, B, h->T, h->w16, h->L, h->pre, h->act, h->Y, h->dY, h->dH, h->dH2, h->grad, h->loss,
+                        h->stream));
+    if (grad) MCU(h, cudaMemcpyAsync(grad, h->grad, sizeof(float) * h->L.nparam, cudaMemcpyDeviceToHost, h->stream));
+    if (loss) MCU(h, cudaMemcpyAsync(loss, h->loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    MCU(h, cudaStreamSynchronize(h->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_mlp_adam_step(psl1_mlp_h h, const float* grad, float lr)
+{
+    if (!h || !grad) return mfail(h, PSL1_ERR_ARG, "bad argument");
+    MCU(h, cudaMemcpyAsync(h->grad, grad, sizeof(float) * h->L.nparam, cudaMemcpyHostToDevice, h->stream));
+    h->adam_t += 1;
+    MCU(h, mlp_adam(h->master, h->grad, h->m, h->v, h->L.nparam, h->adam_t, lr, 0.9f, 0.999f, 1e-8f, h->stream));
+    MCU(h, mlp_refresh_bf16(h->master, h->w16, h->wT, nullptr, h->L, h->stream));
+    MCU(h, cudaStreamSynchronize(h->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_mlp_dataset(psl1_mlp_h mh, psl1_h data, int source, int iters)
+{
+    if (!mh || !data || !(source & (PSL1_DATA_TRAJECTORIES | PSL1_DATA_ITERATES)))
+        return mfail(mh, PSL1_ERR_ARG, "bad argument");
+    if ((source & PSL1_DATA_TRAJECTORIES) && (!data->ser_done || data->ser_kind != PSL1_SERIAL_HYBRID))
+        return mfail(mh, PSL1_ERR_STATE, "trajectory samples need a serial HYBRID solve of the data problem");
+    if ((source & PSL1_DATA_ITERATES) && (!data->u0_set || iters < 1))
+        return mfail(mh, PSL1_ERR_STATE, "iterate samples need u0 and iters >= 1");
+    iters = std::min(iters, data->P);
+    if (data->stream != mh->stream) MCU(mh, cudaStreamSynchronize(data->stream));
+    const int B = data->B, P = data->P, BP = B * P;
+    const int S = ((source & PSL1_DATA_TRAJECTORIES) ? BP : 0) + ((source & PSL1_DATA_ITERATES) ? BP * iters : 0);
+    if (S > mh->Scap) {
+        TRY(malloc_m(mh, &mh->Z, (size_t)S * mh->nin));
+        TRY(malloc_m(mh, &mh->R, (size_t)S * mh->nout));
+        TRY(malloc_m(mh, &mh->valid, (size_t)S));
+        mh->Scap = S;
+    }
+    mh->S = S;
+    MCU(mh, cudaMemsetAsync(mh->Z, 0, sizeof(float) * (size_t)S * mh->nin, mh->stream));
+    MCU(mh, cudaMemsetAsync(mh->R, 0, sizeof(float) * (size_t)S * mh->nout, mh->stream));
+    MCU(mh, cudaMemsetAsync(data->d_status, 0, sizeof(DevStatus), mh->stream));
+    PathArgs run = data->pa;          // the data problem's own coarse propagator
+    PathArgs feat = data->pa;         // feature / sample layout of this network
+    feat.mlp = mh->dev();
+    std::vector<int> valid;
+    long long base = 0;
+    if (source & PSL1_DATA_TRAJECTORIES) {
+        // features and residuals of the plain L1 coarse propagator on S_hyb
+        MCU(mh, cudaMemsetAsync(data->d_counter, 0, sizeof(int), mh->stream));
+        MCU(mh, launch_coarse_dataset(feat, data->d_Us, data->d_units, data->nunits, data->d_counter, mh->Z, mh->R,
+                                      std::min(data->nunits, feat.nslots), mh->stream));
+        for (int s = 0; s < BP; ++s) valid.push_back(s);
+        base = BP;
+    }
+    if (source & PSL1_DATA_ITERATES) {
+        // iterations of parareal on the data problem; after each F stage the pairs
+        // (z(U^k_{0:n}), F_old(n) - G_old(n)) of every slice n >= k become samples
+        std::vector<int> nfirst(B, 0), active(B, 1);
+        double* Uk = data->d_Ua;
+        double* Uk1 = data->d_Ub;
+        MCU(mh, cudaMemcpyAsync(data->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, mh->stream));
+        MCU(mh, launch_coarse_sweep(run, B, data->d_u0, nullptr, Uk, nullptr, data->d_Gold, 1, data->d_nfirst,
+                                    data->d_active, data->d_incr, mh->stream));
+        for (int k = 0; k < iters; ++k) {
+            for (int b = 0; b < B; ++b) nfirst[b] = k;
+            MCU(mh, cudaMemcpyAsync(data->d_nfirst, nfirst.data(), sizeof(int) * B, cudaMemcpyHostToDevice, mh->stream));
+            MCU(mh, cudaMemsetAsync(data->d_counter, 0, sizeof(int), mh->stream));
+            MCU(mh, launch_fstage(run, Uk, data->d_Fv, data->d_units, data->nunits, data->d_counter, data->d_nfirst,
+                                  data->d_active, std::min(data->nunits, run.nslots), mh->stream));
+            MCU(mh, launch_iterate_dataset(feat, B, P, Uk, data->d_Fv, data->d_Gold, data->d_nfirst, mh->Z, mh->R,
+                                           base + (long long)k * BP, mh->stream));
+            MCU(mh, launch_coarse_sweep(run, B, data->d_u0, Uk, Uk1, data->d_Fv, data->d_Gold, 0, data->d_nfirst,
+                                        data->d_active, data->d_incr, mh->stream));
+            std::swap(Uk, Uk1);
+            for (int b = 0; b < B; ++b)
+                for (int n = k; n < P; ++n) valid.push_back((int)(base + (long long)k * BP + (long long)b * P + n));
+        }
+        data->d_Ucur = Uk;
+    }
+    mh->nvalid = (int)valid.size();
+    MCU(mh, cudaMemcpyAsync(mh->valid, valid.data(), sizeof(int) * valid.size(), cudaMemcpyHostToDevice, mh->stream));
+    MCU(mh, mlp_scale_targets(mh->R, S, mh->nvalid, mh->nout, mh->oscale, mh->stream));
+    MCU(mh, cudaStreamSynchronize(mh->stream));
+    DevStatus dst{};
+    MCU(mh, cudaMemcpy(&dst, data->d_status, sizeof dst, cudaMemcpyDeviceToHost));
+    if (dst.code != 0) return mfail(mh, (psl1_status)dst.code, "device error while generating samples");
+    return PSL1_OK;
+}
+
+psl1_status psl1_mlp_train(psl1_mlp_h mh, psl1_h data, int epochs, int batch, float lr, unsigned long long seed,
+                           float* loss_log)
+{
+    if (!mh || epochs < 0 || batch < 1) return mfail(mh, PSL1_ERR_ARG, "bad argument");
+    if (mh->nvalid == 0) {
+        if (!data) return mfail(mh, PSL1_ERR_STATE, "no samples: build a dataset or pass a data problem");
+        TRY(psl1_mlp_dataset(mh, data, PSL1_DATA_TRAJECTORIES, 0));
+    }
+    const int S = mh->nvalid;
+    TRY(ensure_batch(mh, batch));
+    // Adam with a cosine learning-rate decay; each epoch visits the samples in the
+    // order of an affine permutation (a j + c) mod S with gcd(a, S) = 1
+    const int steps = std::max(1, S / batch);
+    const long long total = (long long)epochs * steps;
+    long long it = 0;
+    auto gcd = [](long long x, long long y) {
+        while (y) {
+            long long t = x % y;
+            x = y;
+            y = t;
+        }
+        return x;
+    };
+    unsigned long long rs = seed * 6364136223846793005ULL + 1442695040888963407ULL;
+    for (int ep = 0; ep < epochs; ++ep) {
+        rs = rs * 6364136223846793005ULL + 1442695040888963407ULL;
+        long long pa = (long long)((rs >> 33) % (unsigned long long)S) | 1;
+        while (gcd(pa, S) != 1) pa += 2;
+        long long pc = (long long)((rs >> 13) % (unsigned long long)S);
+        MCU(mh, cudaMemsetAsync(mh->loss, 0, sizeof(float), mh->stream));
+        for (int s = 0; s < steps; ++s, ++it) {
+            float lr_t = 0.5f * lr * (1.0f + cosf(3.14159265f * (float)it / (float)std::max<long long>(total, 1)));
+            MCU(mh, mlp_gather(mh->Z, mh->R, mh->valid, S, mh->nin, mh->nout, batch, pa, pc, (long long)s * batch,
+                               mh->X0, mh->T, mh->stream));
+            MCU(mh, mlp_forward(mh->X0, batch, mh->w16, mh->master, mh->L, mh->pre, mh->act, mh->Y, mh->stream));
+            MCU(mh, mlp_backward(mh->X0, batch, mh->T, mh->w16, mh->L, mh->pre, mh->act, mh->Y, mh->dY, mh->dH,
+                                 mh->dH2, mh->grad, mh->loss, mh->stream));
+            mh->adam_t += 1;
+            MCU(mh, mlp_adam(mh->master, mh->grad, mh->m, mh->v, mh->L.nparam, mh->adam_t, lr_t, 0.9f, 0.999f, 1e-8f,
+                             mh->stream));
+            MCU(mh, mlp_refresh_bf16(mh->master, mh->w16, mh->wT, nullptr, mh->L, mh->stream));
+        }
+        if (loss_log) {
+            float l = 0.f;
+            MCU(mh, cudaMemcpyAsync(&l, mh->loss, sizeof(float), cudaMemcpyDeviceToHost, mh->stream));
+            MCU(mh, cudaStreamSynchronize(mh->stream));
+            loss_log[ep] = l / steps;
+        }
+    }
+    MCU(mh, cudaStreamSynchronize(mh->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_set_coarse(psl1_h h, psl1_mlp_h mh)
+{
+    if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
+    if (!mh) {
+        h->pa.mlp = MlpDev{};
+        return PSL1_OK;
+    }
+    if (mh->stream != h->stream) CU(h, cudaStreamSynchronize(mh->stream));
+    h->pa.mlp = mh->dev();
+    return PSL1_OK;
 }
 
 }  // extern "C"

@@ -22,6 +22,7 @@ struct Carve {
     MixSmem ms;
     PcgSmem cg;
     float* fac;
+    df *mz, *mh0, *mh1;      // learned-correction features and hidden activations (double-float)
 };
 
 template <typename T>
@@ -64,6 +65,9 @@ __device__ __forceinline__ Carve carve(const PathArgs& a, char* base)
     c.cg.pl = at<float>(base, L.cgpl);
     c.cg.dinv = at<float>(base, L.cgdinv);
     c.cg.red2 = at<float>(base, L.cgred);
+    c.mz = at<df>(base, L.mz);
+    c.mh0 = at<df>(base, L.mh0);
+    c.mh1 = at<df>(base, L.mh1);
     c.fac = a.fac_in_smem ? at<float>(base, L.fac)
                           : reinterpret_cast<float*>(a.work + (size_t)blockIdx.x * a.work_stride);
     return c;
@@ -111,6 +115,9 @@ SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int 
     L.cgpl = pcg ? take(4 * (size_t)Kpmax) : -1;
     L.cgdinv = pcg ? take(4 * (size_t)Kpmax) : -1;
     L.cgred = pcg ? take(4 * 2 * (NT / 32)) : -1;
+    L.mz = take(8 * (size_t)MLP_MAX_IN);
+    L.mh0 = take(8 * (size_t)MLP_MAX_WIDTH);
+    L.mh1 = take(8 * (size_t)MLP_MAX_WIDTH);
     L.fac = -1;
     *fac_in_smem = 0;
     if (!f64 && !pcg) {
@@ -207,6 +214,58 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
     __syncthreads();
 }
 
+// Features of the learned correction at coarse node n (cv.cur = U_n,
+// cv.hist = U_n - eta_n after coarse_step), zero for modes beyond K.
+__device__ __forceinline__ double learned_feature(const MlpDev& M, const InstDev& I, int n, const Carve& cv, int i)
+{
+    if (i < M.nU) return i < I.K ? (double)(i + 1) * (i + 1) * cv.cur[i] : 0.0;
+    if (i < M.nU + M.nH) {
+        int k = i - M.nU;
+        return k < I.K ? (double)(k + 1) * (k + 1) * (cv.cur[k] - cv.hist[k]) : 0.0;
+    }
+    return (i == M.nU + M.nH) ? I.alpha : I.dT * n;
+}
+
+// FP32 features (training samples)
+__device__ void learned_features(const MlpDev& M, const InstDev& I, int n, const Carve& cv, float* z)
+{
+    for (int i = threadIdx.x; i < M.nin; i += NT) z[i] = (float)learned_feature(M, I, n, cv, i);
+}
+
+// One dense layer of the single-sample forward inside a coarse step: transposed
+// BF16 weights (exact in FP32), double-float inputs and accumulation, SiLU in
+// FP64.  Parareal stops on the increment of its iterates, so G has to be a
+// smooth function of U far below the tolerance; FP32 inference leaves a
+// rounding floor near 1e-8 in the increments.
+__device__ __forceinline__ void mlp_layer_df(const MlpDev& M, int l, const df* in, df* out, bool silu)
+{
+    const int din = l == 0 ? M.nin : M.width, dout = l == 3 ? M.nout : M.width;
+    const __nv_bfloat16* w = M.wT + M.oT[l];
+    const float* b = M.bias + M.ob[l];
+    for (int o = threadIdx.x; o < dout; o += NT) {
+        dfacc acc{b[o], 0.f};
+        for (int i = 0; i < din; ++i) dfacc_fma(acc, df{__bfloat162float(w[(size_t)i * dout + o]), 0.f}, in[i]);
+        double a = df_to_double(dfacc_result(acc));
+        out[o] = df_from_double(silu ? a / (1.0 + exp(-a)) : a);
+    }
+    __syncthreads();
+}
+
+// G_theta = G_n + s o MLP(z): adds the learned correction to cv.nxt
+__device__ void learned_correction(const PathArgs& a, const InstDev& I, int n, Carve& cv)
+{
+    const MlpDev& M = a.mlp;
+    for (int i = threadIdx.x; i < M.nin; i += NT) cv.mz[i] = df_from_double(learned_feature(M, I, n, cv, i));
+    __syncthreads();
+    mlp_layer_df(M, 0, cv.mz, cv.mh0, true);
+    mlp_layer_df(M, 1, cv.mh0, cv.mh1, true);
+    mlp_layer_df(M, 2, cv.mh1, cv.mh0, true);
+    mlp_layer_df(M, 3, cv.mh0, cv.mh1, false);
+    const int kk = I.K < M.nout ? I.K : M.nout;
+    for (int k = threadIdx.x; k < kk; k += NT) cv.nxt[k] += (double)M.oscale[k] * df_to_double(cv.mh1[k]);
+    __syncthreads();
+}
+
 // G_n of instance ii on U (rows 0..n, global) -> cv.nxt.  History in the
 // difference form U_n - sum_{j=0}^{n-1} b_{n-j} (U_{j+1} - U_j) of Eq. L1Scheme.
 __device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, Carve& cv)
@@ -225,6 +284,79 @@ __device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, C
     int bad = do_step(a, I, cv.cur, cv.hist, I.dT * n, I.muT, cv.nxt, cv);
     if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_COARSE, n);
     check_finite(a, cv.nxt, K, ii, WHERE_COARSE, n);
+    if (a.mlp.on) learned_correction(a, I, n, cv);
+}
+
+// Training samples from a parareal iterate: for every (instance, n >= nfirst):
+// features of U^k_{0:n} and the correction parareal applies there,
+// F_old(n) - G_old(n) = F_n(U^k_{0:n}) - G_n(U^k_{0:n}).  Sample slot:
+// base + ii * P + n (slots n < nfirst are left untouched and not used).
+__global__ void __launch_bounds__(NT) k_iterate_dataset(PathArgs a, const double* Uk, const double* Fv,
+                                                        const double* Gold, const int* nfirst, float* Z, float* R,
+                                                        long long base)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve(a, smem_raw);
+    const MlpDev& M = a.mlp;
+    const int ii = blockIdx.y, n = blockIdx.x;
+    const InstDev& I = a.inst[ii];
+    if (n >= I.P || n < nfirst[ii]) return;
+    const double* U = Uk + I.oU;
+    const double* bF = a.bp + I.oB;
+    for (int k = threadIdx.x; k < I.K; k += NT) {
+        double c = U[(size_t)n * I.K + k], h = c;
+        for (int j = 0; j < n; ++j) h -= bF[n - j] * (U[(size_t)(j + 1) * I.K + k] - U[(size_t)j * I.K + k]);
+        cv.cur[k] = c;
+        cv.hist[k] = h;
+    }
+    __syncthreads();
+    const long long s = base + (long long)ii * I.P + n;
+    learned_features(M, I, n, cv, Z + s * M.nin);
+    for (int k = threadIdx.x; k < M.nout; k += NT) {
+        size_t e = (size_t)I.oPK + (size_t)n * I.K + k;
+        R[s * M.nout + k] = k < I.K ? (float)(Fv[e] - Gold[e]) : 0.f;
+    }
+}
+
+cudaError_t launch_iterate_dataset(const PathArgs& a, int B, int P, const double* Uk, const double* Fv,
+                                   const double* Gold, const int* nfirst, float* Z, float* R, long long base,
+                                   cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    cudaError_t e = cudaFuncSetAttribute(k_iterate_dataset, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid(P, B);
+    k_iterate_dataset<<<grid, NT, sm, s>>>(a, Uk, Fv, Gold, nfirst, Z, R, base);
+    return cudaGetLastError();
+}
+
+// Training samples of the learned correction from a serial S_hyb solution Us:
+// for sample s = (instance ii, node n < P): features z_n and the residual
+// U_{n+1} - G_n(U_{0:n}) of the plain L1 coarse propagator (first nout modes).
+__global__ void __launch_bounds__(NT) k_coarse_dataset(PathArgs a, const double* Us, const int2* units, int nunits,
+                                                       int* counter, float* Z, float* R)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve(a, smem_raw);
+    __shared__ int s_u;
+    const MlpDev& M = a.mlp;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_u = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_u;
+        if (u >= nunits) break;
+        const int ii = units[u].x, n = units[u].y;
+        const InstDev& I = a.inst[ii];
+        const double* U = Us + I.oU;
+        PathArgs plain = a;
+        plain.mlp.on = 0;
+        coarse_step(plain, ii, n, U, cv);
+        const long long s = (long long)ii * I.P + n;
+        learned_features(M, I, n, cv, Z + s * M.nin);
+        for (int k = threadIdx.x; k < M.nout; k += NT)
+            R[s * M.nout + k] = k < I.K ? (float)(U[(size_t)(n + 1) * I.K + k] - cv.nxt[k]) : 0.f;
+    }
 }
 
 __global__ void __launch_bounds__(NT) k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units,
@@ -566,6 +698,17 @@ cudaError_t launch_one_slice(const PathArgs& a, int b, int n, const double* U, d
     cudaError_t e = prep(k_one_slice, sm);
     if (e != cudaSuccess) return e;
     k_one_slice<<<1, NT, sm, s>>>(slot(a, 3), b, n, U, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_dataset(const PathArgs& a, const double* Us, const int2* units, int nunits, int* counter,
+                                  float* Z, float* R, int grid, cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    cudaError_t e = prep(k_coarse_dataset, sm);
+    if (e != cudaSuccess) return e;
+    if (grid > a.nslots) grid = a.nslots;
+    k_coarse_dataset<<<grid, NT, sm, s>>>(slot(a, 3), Us, units, nunits, counter, Z, R);
     return cudaGetLastError();
 }
 

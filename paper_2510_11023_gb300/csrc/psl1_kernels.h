@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "psl1_device.cuh"
+#include "psl1_mlp.h"
 
 namespace psl1 {
 
@@ -18,6 +19,7 @@ struct SmemLayout {
     int cur, hist, nxt, F, v, wp, wm, fp, fm, g, bad;     // FP64 path (+ common)
     int cdf, wpd, wmd, fpd, fmd, gdf, ydf, x, rhs, z, red, fac;   // FP32-pipe path
     int cgx, cgr, cgp, cgq, cgpl, cgdinv, cgred;                 // PCG inner solver
+    int mz, mh0, mh1;                                            // learned correction inference
     int total;
 };
 
@@ -40,6 +42,7 @@ struct PathArgs {
     int inner;               // INNER_CHOL or INNER_PCG (FP32-pipe paths)
     double* flops;           // algorithmic FLOP accumulators (by slot), may be null
     int flop_slot;           // 0 F stage, 1 coarse sweeps, 2 serial solvers, 3 single pieces
+    MlpDev mlp;              // learned coarse correction (mlp.on = 0: plain L1 G)
 };
 
 SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem);
@@ -68,6 +71,15 @@ cudaError_t launch_one_step(const PathArgs& a, int b, const double* c, const dou
                             double mu, double* out, cudaStream_t s);
 cudaError_t launch_one_slice(const PathArgs& a, int b, int n, const double* U, double* V, cudaStream_t s);
 cudaError_t launch_one_coarse(const PathArgs& a, int b, int n, const double* U, double* out, cudaStream_t s);
+
+// Learned-correction training samples from a serial S_hyb solution (persistent CTAs over units).
+cudaError_t launch_coarse_dataset(const PathArgs& a, const double* Us, const int2* units, int nunits, int* counter,
+                                  float* Z, float* R, int grid, cudaStream_t s);
+
+// Learned-correction samples (z(U^k_{0:n}), F_old(n) - G_old(n)) from one parareal iterate.
+cudaError_t launch_iterate_dataset(const PathArgs& a, int B, int P, const double* Uk, const double* Fv,
+                                   const double* Gold, const int* nfirst, float* Z, float* R, long long base,
+                                   cudaStream_t s);
 
 // Single slice with scratch from a fixed device array (no allocation).
 constexpr long long NOALLOC_SCRATCH_DOUBLES = 512 * 1024;   // 4 MiB

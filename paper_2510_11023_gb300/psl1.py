@@ -23,6 +23,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOT_SPD", -3: "ERR_NONFINITE", -4: "E
           -6: "ERR_NOT_CONVERGED", -7: "ERR_STATE", -8: "ERR_NOMEM"}
 
 _D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
 _I = ctypes.POINTER(ctypes.c_int)
 
 
@@ -75,6 +76,20 @@ SIGNATURES = {
     "psl1_fine_slice_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                ctypes.c_void_p]),
     "psl1_probe_peaks": (ctypes.c_int, [_D, _D]),
+    "psl1_mlp_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_ulonglong, ctypes.c_void_p]),
+    "psl1_mlp_nparams": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "psl1_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, _F, _F]),
+    "psl1_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, _F, _F]),
+    "psl1_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _F, _F]),
+    "psl1_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _F, _F, _F, _F]),
+    "psl1_mlp_adam_step": (ctypes.c_int, [ctypes.c_void_p, _F, ctypes.c_float]),
+    "psl1_mlp_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                      ctypes.c_ulonglong, _F]),
+    "psl1_set_coarse": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "psl1_mlp_dataset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "psl1_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "psl1_mlp_destroy": (None, [ctypes.c_void_p]),
     "psl1_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "psl1_destroy": (None, [ctypes.c_void_p]),
 }
@@ -270,8 +285,99 @@ class Problem:
         """F_n on caller-owned device arrays (pointers), without any allocation."""
         _chk(self.L.psl1_fine_slice_noalloc(self.h, b, n, ctypes.c_void_p(d_U), ctypes.c_void_p(d_V)), self.h)
 
+    def set_coarse(self, mlp: "MLP | None"):
+        """Attach a learned coarse correction (None: the plain L1 coarse propagator)."""
+        _chk(self.L.psl1_set_coarse(self.h, mlp.h if mlp is not None else None), self.h)
+        self._mlp = mlp   # keep it alive while attached
+
     def coarse_step(self, b: int, n: int, U) -> np.ndarray:
         U = np.ascontiguousarray(U, dtype=np.float64)
         out = np.zeros(self.K[b])
         _chk(self.L.psl1_coarse_step(self.h, b, n, _dp(U), _dp(out)), self.h)
         return out
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(_F)
+
+
+class MLP:
+    """The learned coarse correction (wraps one psl1_mlp handle)."""
+
+    def __init__(self, nU: int = 128, nH: int = 32, width: int = 512, nout: int = 128, seed: int = 0,
+                 stream: int | None = None):
+        self.L = load()
+        h = ctypes.c_void_p()
+        st = self.L.psl1_mlp_create(ctypes.byref(h), nU, nH, width, nout, ctypes.c_ulonglong(seed),
+                                    ctypes.c_void_p(stream) if stream else None)
+        if st != 0:
+            raise PSL1Error(st, (self.L.psl1_mlp_last_error(None) or b"").decode())
+        self.h = h
+        self.nU, self.nH, self.width, self.nout = nU, nH, width, nout
+        self.nin = nU + nH + 2
+        n = ctypes.c_longlong(0)
+        self._chk(self.L.psl1_mlp_nparams(self.h, ctypes.byref(n)))
+        self.nparams = n.value
+
+    def _chk(self, st):
+        if st != 0:
+            raise PSL1Error(st, (self.L.psl1_mlp_last_error(self.h) or b"").decode())
+
+    def close(self):
+        if self.h:
+            self.L.psl1_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def get_params(self):
+        p = np.zeros(self.nparams, dtype=np.float32)
+        s = np.zeros(self.nout, dtype=np.float32)
+        self._chk(self.L.psl1_mlp_get_params(self.h, _fp(p), _fp(s)))
+        return p, s
+
+    def set_params(self, params=None, oscale=None):
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        s = None if oscale is None else np.ascontiguousarray(oscale, dtype=np.float32)
+        self._chk(self.L.psl1_mlp_set_params(self.h, _fp(p) if p is not None else None,
+                                             _fp(s) if s is not None else None))
+
+    def forward(self, z) -> np.ndarray:
+        z = np.ascontiguousarray(np.atleast_2d(z), dtype=np.float32)
+        y = np.zeros((z.shape[0], self.nout), dtype=np.float32)
+        self._chk(self.L.psl1_mlp_forward(self.h, z.shape[0], _fp(z), _fp(y)))
+        return y
+
+    def loss_grad(self, z, t):
+        z = np.ascontiguousarray(np.atleast_2d(z), dtype=np.float32)
+        t = np.ascontiguousarray(np.atleast_2d(t), dtype=np.float32)
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = ctypes.c_float(0)
+        self._chk(self.L.psl1_mlp_loss_grad(self.h, z.shape[0], _fp(z), _fp(t), _fp(g), ctypes.byref(loss)))
+        return g, loss.value
+
+    def adam_step(self, grad, lr: float):
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        self._chk(self.L.psl1_mlp_adam_step(self.h, _fp(g), float(lr)))
+
+    def dataset(self, data: Problem, trajectories: bool = False, iterates: int = 0):
+        """Build the training set from `data`: S_hyb trajectory samples and/or the
+        samples of `iterates` parareal iterations (see psl1_mlp_dataset)."""
+        src = (1 if trajectories else 0) | (2 if iterates > 0 else 0)
+        self._chk(self.L.psl1_mlp_dataset(self.h, data.h, src, int(iterates)))
+
+    def train(self, data: Problem, epochs: int = 100, batch: int = 512, lr: float = 1e-3, seed: int = 0):
+        log = np.zeros(max(epochs, 1), dtype=np.float32)
+        self._chk(self.L.psl1_mlp_train(self.h, data.h, int(epochs), int(batch), float(lr),
+                                        ctypes.c_ulonglong(seed), _fp(log)))
+        return log[:epochs]
