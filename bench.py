@@ -41,12 +41,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp32"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "fp32"])
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--seed", type=int, default=20251011)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--coarse", default="auto", choices=["auto", "l1", "learned"],
+                    help="coarse propagator; auto: the faster to rel err 1e-8 in warm-up")
+    ap.add_argument("--train-batch", type=int, default=128, help="instances the learned correction trains on")
+    ap.add_argument("--train-iters", type=int, default=8)
+    ap.add_argument("--train-epochs", type=int, default=40)
     ap.add_argument("--reference", default="fp64", choices=["fp64", "same"],
                     help="precision of the serial S_hyb the error is measured against (same: profiling runs)")
     return ap.parse_args()
@@ -242,16 +247,46 @@ def main():
         serial_ms = serial_fp64_ms
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
-    # warm-up: pick the stopping tolerance that reaches the target error
-    tol, err = 1e-8, None
-    for w in range(max(args.warmup, 1)):
+    # learned coarse correction, trained offline (not timed) on another seed of the
+    # same instance distribution from the pairs parareal computes
+    mlp, train_info = None, None
+    if args.coarse in ("auto", "learned"):
+        t0 = time.perf_counter()
+        twl = workloads.cfg2(B=args.train_batch, seed=args.seed + 7919 + dist.rank)
+        with psl1.Problem(twl, precision=args.precision, stream=stream.cuda_stream) as data:
+            mlp = psl1.MLP(128, 32, 512, 128, seed=1, stream=stream.cuda_stream)
+            mlp.dataset(data, iterates=args.train_iters)
+            log = mlp.train(data, epochs=args.train_epochs, batch=1024, lr=1e-3, seed=2)
+        torch.cuda.synchronize()
+        train_info = {"seconds": time.perf_counter() - t0, "instances": twl.B, "iterates": args.train_iters,
+                      "epochs": args.train_epochs, "loss_first": float(log[0]), "loss_last": float(log[-1]),
+                      "seed": args.seed + 7919}
+
+    def tune(coarse):
+        """Loosest increment tolerance that reaches the target error; its solve time."""
+        pr.set_coarse(mlp if coarse == "learned" else None)
         pr.set_u0_dev(d_u0.data_ptr())
-        pr.solve_parareal(tol=tol, allow_not_converged=True)
-        err = rel_err(pr.get_coeffs("parareal"), S)
-        while err > TARGET and tol > 1e-13:
-            tol /= 3.0
-            pr.solve_parareal(tol=tol, allow_not_converged=True)
-            err = rel_err(pr.get_coeffs("parareal"), S)
+        tol_ = 1.6e-7          # halved until the iterate meets the target error
+        while True:
+            pr.solve_parareal(tol=tol_, allow_not_converged=True)
+            if rel_err(pr.get_coeffs("parareal"), S) <= TARGET or tol_ < 1e-13:
+                break
+            tol_ /= 2.0
+        for _ in range(max(args.warmup - 1, 0)):
+            pr.solve_parareal(tol=tol_, allow_not_converged=True)
+        e0.record(stream)
+        pr.solve_parareal(tol=tol_, allow_not_converged=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"tol": tol_, "ms": e0.elapsed_time(e1), "iterations": int(pr.get_iterations().max()),
+                "rel_err": rel_err(pr.get_coeffs("parareal"), S)}
+
+    cands = {}
+    for c in (["l1", "learned"] if args.coarse == "auto" else [args.coarse]):
+        cands[c] = tune(c)
+    coarse = min(cands, key=lambda c: cands[c]["ms"])
+    pr.set_coarse(mlp if coarse == "learned" else None)
+    tol = cands[coarse]["tol"]
 
     # timed region
     dist.barrier()
@@ -330,12 +365,15 @@ def main():
                        "l2": "flushed (256 MB write) before every timed step", "seed": args.seed},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "rel_err_vs_serial_fp64": err, "stop_tol": tol, "iterations": iters_all,
+            "coarse_propagator": coarse, "coarse_candidates": cands, "learned_training": train_info,
             "serial_fp64_ms": serial_fp64_ms, "serial_ms": serial_ms,
             "speedup_vs_serial_fp64": serial_fp64_ms / ms_step, "speedup_vs_serial_same_precision": serial_ms / ms_step,
             "measured_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf}, "wall_s": wall}
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
     pr.close()
+    if mlp is not None:
+        mlp.close()
     dist.close()
 
 
