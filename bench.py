@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=0.0,
+                    help="CPU seconds per reference-arm step (0: about 2 minutes in total)")
     ap.add_argument("--coarse", default="auto", choices=["auto", "l1", "learned"],
                     help="coarse propagator; auto: the faster to rel err 1e-8 in warm-up")
     ap.add_argument("--train-batch", type=int, default=128, help="instances the learned correction trains on")
@@ -182,7 +184,7 @@ def reference_arm(args, dist: Dist):
     if dist.rank != 0:
         return
     wl = workloads.cfg2(B=args.batch, seed=args.seed)
-    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    per_step = args.ref_step_seconds or max(2.0, 120.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         oracle_throughput(wl, None, per_step / 4)
     vals, secs = [], []
