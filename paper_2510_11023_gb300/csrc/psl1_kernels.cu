@@ -65,6 +65,9 @@ __device__ __forceinline__ Carve carve(const PathArgs& a, char* base)
     c.cg.pl = at<float>(base, L.cgpl);
     c.cg.dinv = at<float>(base, L.cgdinv);
     c.cg.red2 = at<float>(base, L.cgred);
+    c.cg.gs = at<float>(base, L.cggs);
+    c.cg.gh = at<float>(base, L.cggh);
+    c.cg.part = at<float>(base, L.cgpart);
     c.mz = at<df>(base, L.mz);
     c.mh0 = at<df>(base, L.mh0);
     c.mh1 = at<df>(base, L.mh1);
@@ -115,6 +118,9 @@ SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int 
     L.cgpl = pcg ? take(4 * (size_t)Kpmax) : -1;
     L.cgdinv = pcg ? take(4 * (size_t)Kpmax) : -1;
     L.cgred = pcg ? take(4 * 2 * (NT / 32)) : -1;
+    L.cggs = pcg ? take(4 * (size_t)(2 * Kmax + 8)) : -1;
+    L.cggh = pcg ? take(4 * (size_t)(2 * Kmax + 8)) : -1;
+    L.cgpart = pcg ? take(4 * (size_t)(4 * NT)) : -1;
     L.mz = take(8 * (size_t)MLP_MAX_IN);
     L.mh0 = take(8 * (size_t)MLP_MAX_WIDTH);
     L.mh1 = take(8 * (size_t)MLP_MAX_WIDTH);

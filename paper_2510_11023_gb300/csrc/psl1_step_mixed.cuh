@@ -325,7 +325,61 @@ constexpr float PCG_RTOL = 1e-6f;
 struct PcgSmem {
     float *x, *r, *p, *q, *pl, *dinv;   // Kp each
     float* red2;                         // 2 * NT/32
+    float *gs, *gh;                      // 2 Kmax + 8 each: moment windows
+    float* part;                         // 4 NT: partial sums of the blocked product
 };
+
+// acc_k = sum_l (g_|k-l| + g_{k+l+2}) pl_l  ->  cg.q[k], k < K.
+// Each thread owns four consecutive outputs and a chunk of the columns l; the
+// Toeplitz and Hankel windows slide through registers (one new shared-memory
+// load each per column instead of eight), and the chunks are summed at the end.
+__device__ void th_product32(int K, PcgSmem& cg)
+{
+    const int ng = (K + 3) / 4;
+    int S = NT / ng;
+    S = S < 1 ? 1 : (S > 16 ? 16 : S);
+    const int L = (K + S - 1) / S;
+    const int t = threadIdx.x;
+    for (int task = t; task < ng * S; task += NT) {
+        const int grp = task / S, c = task % S;
+        const int k0 = 4 * grp;
+        const int l0 = c * L, l1 = (l0 + L < K) ? l0 + L : K;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (l0 < l1) {
+            const float* gs = cg.gs + K + k0;   // T_r(l) = gs[r - l]
+            const float* gh = cg.gh + k0 + 2;   // H_r(l) = gh[r + l]
+            float T0 = gs[-l0], T1 = gs[1 - l0], T2 = gs[2 - l0], T3 = gs[3 - l0];
+            float H0 = gh[l0], H1 = gh[l0 + 1], H2 = gh[l0 + 2], H3 = gh[l0 + 3];
+            for (int l = l0; l < l1; ++l) {
+                const float p = cg.pl[l];
+                a0 = fmaf(T0 + H0, p, a0);
+                a1 = fmaf(T1 + H1, p, a1);
+                a2 = fmaf(T2 + H2, p, a2);
+                a3 = fmaf(T3 + H3, p, a3);
+                T3 = T2;
+                T2 = T1;
+                T1 = T0;
+                T0 = gs[-(l + 1)];
+                H0 = H1;
+                H1 = H2;
+                H2 = H3;
+                H3 = gh[l + 4];
+            }
+        }
+        float* out = cg.part + c * (4 * ng) + k0;
+        out[0] = a0;
+        out[1] = a1;
+        out[2] = a2;
+        out[3] = a3;
+    }
+    __syncthreads();
+    for (int k = t; k < K; k += NT) {
+        float s = 0.f;
+        for (int c = 0; c < S; ++c) s += cg.part[c * (4 * ng) + k];
+        cg.q[k] = s;
+    }
+    __syncthreads();
+}
 
 __device__ __forceinline__ float2 block_sum2(float a, float b, float* red2)
 {
@@ -365,6 +419,13 @@ __device__ void pcg32(const InstDev& I, double mu, MixSmem& ms, PcgSmem& cg, int
         return;
     }
     const float rs = 1.0f / rmax;
+    // FP32 windows of the moments for the register-blocked product:
+    // gs[j] = g_|j-K| (Toeplitz part), gh[s] = g_s (Hankel part), zero padded
+    for (int j = tid; j < 2 * K + 8; j += NT) {
+        int d = j > K ? j - K : K - j;
+        cg.gs[j] = j <= 2 * K ? g[d].hi : 0.f;
+        cg.gh[j] = j <= 2 * K ? g[j].hi : 0.f;
+    }
     float rz = 0.f, rr = 0.f;
     for (int k = tid; k < K; k += NT) {
         float d = 1.0f + sc * (float)((k + 1) * (k + 1)) * (g[0].hi + g[2 * k + 2].hi);
@@ -384,14 +445,10 @@ __device__ void pcg32(const InstDev& I, double mu, MixSmem& ms, PcgSmem& cg, int
     for (int it = 0; it < maxit && s0.y > 0.f; ++it) {
         if (tid == 0) ms.flag[1] += 1;
         // q = M p, and p.q
+        th_product32(K, cg);
         float pq = 0.f;
         for (int k = tid; k < K; k += NT) {
-            float acc = 0.f;
-            for (int l = 0; l < K; ++l) {
-                int d = k > l ? k - l : l - k;
-                acc = fmaf(g[d].hi + g[k + l + 2].hi, cg.pl[l], acc);
-            }
-            float q = cg.p[k] + sc * (float)(k + 1) * acc;
+            float q = cg.p[k] + sc * (float)(k + 1) * cg.q[k];
             cg.q[k] = q;
             pq += cg.p[k] * q;
         }
