@@ -58,10 +58,14 @@ typedef enum {
 
 /* Precision of the solve (the history sums, L1 weights and parareal
  * correction are FP64 in every mode).
- *  FP64 : plain FP64 everywhere (transforms, assembly, Cholesky).
- *  MIXED: FP32-pair ("double-float") transforms and residuals, FP32 Cholesky
- *         factor with iterative refinement against the FP64-accurate operator.
- *  FP32 : FP32 transforms, assembly and Cholesky; no refinement.            */
+ *  FP64 : plain FP64 everywhere.  1D: transforms, assembly, Cholesky.  2D:
+ *         sum-factorised (matrix-free) operator, Jacobi-preconditioned
+ *         conjugate gradients to a relative residual of 1e-14.
+ *  MIXED: FP32-pair ("double-float") transforms and residuals, an FP32 inner
+ *         solver (conjugate gradients) inside iterative refinement against
+ *         the FP64-accurate operator.
+ *  FP32 : FP32 coefficient functions and a single FP32 inner solve; no
+ *         refinement.                                                       */
 enum { PSL1_PREC_FP64 = 0, PSL1_PREC_MIXED = 1, PSL1_PREC_FP32 = 2 };
 
 /* Serial solvers.
@@ -83,8 +87,9 @@ enum { PSL1_SERIAL_HYBRID = 0, PSL1_SERIAL_UNIFORM = 1, PSL1_SERIAL_COARSE = 2 }
  *   S2: u = (1 + t^2) sin(pi x)/(2 - cos pi x)  with D = d0 + d3 sin(pi x)
  * on (0,1) (1D only).                                                       */
 typedef struct {
-    int dim;          /* 1 or 2                                               */
-    int modes[2];     /* Mx, My (My unused in 1D); 1 <= Mx*My <= 4096         */
+    int dim;          /* 1 or 2; every instance of a handle has the same dim  */
+    int modes[2];     /* Mx, My (My unused in 1D); 1D: Mx <= 512;
+                         2D: Mx, My <= 64 (K = Mx*My <= 4096)                  */
     int qnodes[2];    /* Qx, Qy Gauss-Legendre nodes; 0 selects 2*modes; even */
     int nsteps;       /* N: total fine L1 steps on [0,T]; a multiple of P     */
     double alpha;     /* fractional order, 0 < alpha <= 1                      */
@@ -249,7 +254,8 @@ psl1_status psl1_mlp_train(psl1_mlp_h mh, psl1_h data, int epochs, int batch, fl
                            unsigned long long seed, float* loss_log);
 /* Use the learned correction in every coarse propagator of h (coarse sweeps,
  * G_old, psl1_coarse_step); NULL restores the plain L1 G.  mh must outlive
- * its use by h.                                                            */
+ * its use by h.  The correction is defined for 1D instances: a 2D handle
+ * (here, and as `data` of psl1_mlp_dataset) gives PSL1_ERR_ARG.             */
 psl1_status psl1_set_coarse(psl1_h h, psl1_mlp_h mh);
 const char* psl1_mlp_last_error(psl1_mlp_h mh);
 void psl1_mlp_destroy(psl1_mlp_h mh);

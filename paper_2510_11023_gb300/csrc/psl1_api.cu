@@ -167,12 +167,19 @@ void psl1_destroy(psl1_h h)
 
 static psl1_status validate(const psl1_instance& d, int P, int b)
 {
-    if (d.dim != 1) return fail(nullptr, PSL1_ERR_ARG, "instance %d: dim must be 1 in this build", b);
-    int Mx = d.modes[0];
-    if (Mx < 1 || Mx > KMAX_1D) return fail(nullptr, PSL1_ERR_ARG, "instance %d: modes %d outside [1,%d]", b, Mx, KMAX_1D);
-    int Q = d.qnodes[0] ? d.qnodes[0] : 2 * Mx;
-    if (Q < 2 || (Q & 1) || Q > 4 * KMAX_1D)
-        return fail(nullptr, PSL1_ERR_ARG, "instance %d: quadrature nodes %d must be even in [2,%d]", b, Q, 4 * KMAX_1D);
+    if (d.dim != 1 && d.dim != 2) return fail(nullptr, PSL1_ERR_ARG, "instance %d: dim must be 1 or 2", b);
+    const int mmax = d.dim == 1 ? KMAX_1D : MMAX_2D;
+    for (int ax = 0; ax < d.dim; ++ax) {
+        int M = d.modes[ax];
+        if (M < 1 || M > mmax)
+            return fail(nullptr, PSL1_ERR_ARG, "instance %d: modes[%d] = %d outside [1,%d]", b, ax, M, mmax);
+        int Q = d.qnodes[ax] ? d.qnodes[ax] : 2 * M;
+        if (Q < 2 || (Q & 1) || Q > 4 * mmax)
+            return fail(nullptr, PSL1_ERR_ARG, "instance %d: quadrature nodes[%d] = %d must be even in [2,%d]", b, ax,
+                        Q, 4 * mmax);
+        if (!(d.hi[ax] > d.lo[ax]) || !std::isfinite(d.lo[ax]) || !std::isfinite(d.hi[ax]))
+            return fail(nullptr, PSL1_ERR_ARG, "instance %d: empty domain along axis %d", b, ax);
+    }
     if (d.nsteps < P || d.nsteps % P)
         return fail(nullptr, PSL1_ERR_ARG, "instance %d: nsteps %d must be a positive multiple of P=%d", b, d.nsteps, P);
     if (!(d.alpha > 0.0 && d.alpha <= 1.0)) return fail(nullptr, PSL1_ERR_ARG, "instance %d: alpha must be in (0,1]", b);
@@ -193,6 +200,9 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     if (precision != PSL1_PREC_FP64 && precision != PSL1_PREC_MIXED && precision != PSL1_PREC_FP32)
         return fail(nullptr, PSL1_ERR_ARG, "unknown precision %d", precision);
     for (int b = 0; b < batch; ++b) TRY(validate(in[b], P, b));
+    for (int b = 1; b < batch; ++b)
+        if (in[b].dim != in[0].dim)
+            return fail(nullptr, PSL1_ERR_ARG, "instance %d: all instances of a handle must have the same dim", b);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev < 1)
@@ -226,22 +236,75 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         if (s_ != PSL1_OK) return bail(s_);     \
     } while (0)
 
-    // tables shared by instances with the same (Mx, Qx, box)
+    // tables shared by instances (and axes) with the same (M, Q, interval)
     std::map<std::tuple<int, int, double, double>, int> tabid;
     std::vector<TableJob> jobs;
+    auto table_for = [&](int M, int Q, double lo, double hi) {
+        auto key = std::make_tuple(M, Q, lo, hi);
+        auto it = tabid.find(key);
+        if (it != tabid.end()) return it->second;
+        TabDev t{};
+        t.Mx = M;
+        t.Qx = Q;
+        t.Qh = Q / 2;
+        long long o = h->tabElems;
+        const long long mq = (long long)t.Mx * t.Qh;
+        t.oX = o;
+        o += t.Qh;
+        t.oWq = o;
+        o += t.Qh;
+        t.oAux = o;
+        o += 4LL * t.Qh;
+        t.oSt = o;
+        o += mq;
+        t.oS = o;
+        o += mq;
+        t.oC = o;
+        o += (long long)t.Qh * (2 * t.Mx + 1);
+        t.oStd = o;
+        o += mq;
+        t.oSd = o;
+        o += mq;
+        t.oCd = o;
+        o += (long long)t.Qh * (2 * t.Mx + 1);
+        t.oDt = o;
+        o += mq;
+        t.oDtd = o;
+        o += mq;
+        t.oSt32 = o;
+        o += (mq + 1) / 2;
+        t.oDt32 = o;
+        o += (mq + 1) / 2;
+        t.oAux2 = o;
+        o += 2LL * t.Qh;
+        h->tabElems = o;
+        int id = (int)h->tabs.size();
+        h->tabs.push_back(t);
+        tabid[key] = id;
+        TableJob j{};
+        j.Mx = t.Mx;
+        j.Qh = t.Qh;
+        j.lo = lo;
+        j.hi = hi;
+        jobs.push_back(j);
+        return id;
+    };
     h->inst.resize(batch);
+    long long nT2 = 0, nN2 = 0, ntab2 = 0;
     for (int b = 0; b < batch; ++b) {
         const psl1_instance& d = in[b];
         InstDev& I = h->inst[b];
         memset(&I, 0, sizeof I);
-        I.dim = 1;
+        I.dim = d.dim;
         I.Mx = d.modes[0];
-        I.My = 1;
-        I.K = I.Mx;
+        I.My = d.dim == 2 ? d.modes[1] : 1;
+        I.K = I.Mx * I.My;
         I.nb = (I.K + TILE - 1) / TILE;
         I.Kp = I.nb * TILE;
         I.Q = d.qnodes[0] ? d.qnodes[0] : 2 * I.Mx;
         I.Qh = I.Q / 2;
+        I.Qy = d.dim == 2 ? (d.qnodes[1] ? d.qnodes[1] : 2 * I.My) : 1;
+        I.Qhy = I.Qy / 2;
         I.N = d.nsteps;
         I.P = P;
         I.m = I.N / P;
@@ -257,45 +320,16 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
             I.dpar[i] = d.dpar[i];
             I.fpar[i] = d.fpar[i];
         }
-        auto key = std::make_tuple(I.Mx, I.Q, I.lo0, I.hi0);
-        auto it = tabid.find(key);
-        if (it == tabid.end()) {
-            TabDev t{};
-            t.Mx = I.Mx;
-            t.Qx = I.Q;
-            t.Qh = I.Qh;
-            long long o = h->tabElems;
-            t.oX = o;
-            o += t.Qh;
-            t.oWq = o;
-            o += t.Qh;
-            t.oAux = o;
-            o += 4LL * t.Qh;
-            t.oSt = o;
-            o += (long long)t.Mx * t.Qh;
-            t.oS = o;
-            o += (long long)t.Qh * t.Mx;
-            t.oC = o;
-            o += (long long)t.Qh * (2 * t.Mx + 1);
-            t.oStd = o;
-            o += (long long)t.Mx * t.Qh;
-            t.oSd = o;
-            o += (long long)t.Qh * t.Mx;
-            t.oCd = o;
-            o += (long long)t.Qh * (2 * t.Mx + 1);
-            h->tabElems = o;
-            int id = (int)h->tabs.size();
-            h->tabs.push_back(t);
-            tabid[key] = id;
-            TableJob j{};
-            j.Mx = t.Mx;
-            j.Qh = t.Qh;
-            j.lo = I.lo0;
-            j.hi = I.hi0;
-            jobs.push_back(j);
-            I.tab = id;
+        I.tab = table_for(I.Mx, I.Q, I.lo0, I.hi0);
+        if (I.dim == 2) {
+            I.lo1 = d.lo[1];
+            I.hi1 = d.hi[1];
+            I.tabY = table_for(I.My, I.Qy, I.lo1, I.hi1);
+            nT2 = std::max(nT2, (long long)I.Mx * (I.Qy + 1));
+            nN2 = std::max(nN2, (long long)I.Q * I.Qy);
+            ntab2 = std::max(ntab2, (long long)I.Mx * I.Qh + (long long)I.My * I.Qhy);
         } else {
-            I.tab = it->second;
+            I.tabY = I.tab;
         }
         I.Nb = std::max(std::max(I.N, P), I.m) + 1;
         I.oK = h->sumK;
@@ -320,7 +354,15 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int fac_in_smem = 0;
     const int inner = INNER_PCG;
-    SmemLayout lay = make_layout(precision, inner, h->Kmax, h->Kpmax, h->Qhmax, max_smem - 1024, &fac_in_smem);
+    const bool two_d = in[0].dim == 2;
+    SmemLayout lay{};
+    Layout2D lay2{};
+    if (two_d) {
+        lay2 = make_layout2d(precision, h->Kmax, nT2, nN2, ntab2, max_smem - 1024);
+        lay.total = lay2.smem;
+    } else {
+        lay = make_layout(precision, inner, h->Kmax, h->Kpmax, h->Qhmax, max_smem - 1024, &fac_in_smem);
+    }
     if (lay.total > max_smem - 1024) {
         g_create_error = "instance too large for the shared-memory layout";
         psl1_destroy(h);
@@ -343,7 +385,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     CTRY(dalloc(h, &h->d_status, 1));
     CTRY(dalloc(h, &h->d_flops, 4));
     // per-slot factor workspace: FP64 factor, or the FP32 factor when it does not fit in shared memory
-    long long work_stride = precision == PSL1_PREC_FP64 ? bp_elems(nbmax, TILE)
+    long long work_stride = two_d ? std::max(1LL, (lay2.gbytes + 255) / 256 * 32)   // 256-byte aligned slots
+                            : precision == PSL1_PREC_FP64 ? bp_elems(nbmax, TILE)
                             : (fac_in_smem || inner == INNER_PCG) ? 1
                                                          : (bp_elems(nbmax, MIX_LDB) + 1) / 2;
     long long ring_stride = (long long)h->mmax * h->Kmax;
@@ -355,7 +398,11 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         for (int n = 0; n < P; ++n) units.push_back(make_int2(b, n));
     std::stable_sort(units.begin(), units.end(), [&](int2 x, int2 y) {
         const InstDev &a = h->inst[x.x], &c = h->inst[y.x];
-        double ca = (double)a.m * a.K * a.K * a.K, cc = (double)c.m * c.K * c.K * c.K;
+        // cost per step: K^3 (1D), K (Qx + Qy) per operator application (2D)
+        auto cost = [](const InstDev& I) {
+            return I.dim == 2 ? (double)I.m * I.K * (I.Q + I.Qy) : (double)I.m * I.K * I.K * I.K;
+        };
+        double ca = cost(a), cc = cost(c);
         return ca > cc;
     });
     h->nunits = (int)units.size();
@@ -371,6 +418,11 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         jobs[t].Std = h->d_tp + T.oStd;
         jobs[t].Sd = h->d_tp + T.oSd;
         jobs[t].Cd = h->d_tp + T.oCd;
+        jobs[t].Dt = h->d_tp + T.oDt;
+        jobs[t].Dtd = h->d_tp + T.oDtd;
+        jobs[t].St32 = h->d_tp + T.oSt32;
+        jobs[t].Dt32 = h->d_tp + T.oDt32;
+        jobs[t].aux2 = h->d_tp + T.oAux2;
     }
     auto cu = [&](cudaError_t e2, const char* what) -> psl1_status {
         if (e2 != cudaSuccess) return fail(h, PSL1_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e2));
@@ -412,6 +464,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.inner = inner;
     a.flops = h->d_flops;
     a.flop_slot = 3;
+    a.dim2 = two_d ? 1 : 0;
+    a.L2 = lay2;
     h->iters.assign(batch, 0);
     h->errlog.assign(batch, {});
     h->d_Ucur = h->d_Ua;
@@ -738,7 +792,8 @@ psl1_status psl1_fine_slice_noalloc(psl1_h h, int b, int n, const double* d_U, d
         return fail(h, PSL1_ERR_ARG, "bad argument");
     const InstDev& I = h->inst[b];
     long long ring = (long long)I.m * I.K;
-    long long work = h->prec == PSL1_PREC_FP64 ? bp_elems(I.nb, TILE)
+    long long work = h->pa.dim2 ? h->pa.work_stride   // 2D working arrays outside shared memory
+                     : h->prec == PSL1_PREC_FP64 ? bp_elems(I.nb, TILE)
                      : (h->pa.fac_in_smem || h->pa.inner == INNER_PCG) ? 0
                                                 : (bp_elems(I.nb, MIX_LDB) + 1) / 2;
     if (ring + work > NOALLOC_SCRATCH_DOUBLES)
@@ -995,6 +1050,7 @@ psl1_status psl1_mlp_dataset(psl1_mlp_h mh, psl1_h data, int source, int iters)
         return mfail(mh, PSL1_ERR_STATE, "trajectory samples need a serial HYBRID solve of the data problem");
     if ((source & PSL1_DATA_ITERATES) && (!data->u0_set || iters < 1))
         return mfail(mh, PSL1_ERR_STATE, "iterate samples need u0 and iters >= 1");
+    if (data->pa.dim2) return mfail(mh, PSL1_ERR_ARG, "the learned coarse correction is defined for 1D instances");
     iters = std::min(iters, data->P);
     if (data->stream != mh->stream) MCU(mh, cudaStreamSynchronize(data->stream));
     const int B = data->B, P = data->P, BP = B * P;
@@ -1117,6 +1173,7 @@ psl1_status psl1_set_coarse(psl1_h h, psl1_mlp_h mh)
         h->pa.mlp = MlpDev{};
         return PSL1_OK;
     }
+    if (h->pa.dim2) return fail(h, PSL1_ERR_ARG, "the learned coarse correction is defined for 1D instances");
     if (mh->stream != h->stream) CU(h, cudaStreamSynchronize(mh->stream));
     h->pa.mlp = mh->dev();
     return PSL1_OK;

@@ -15,6 +15,7 @@ namespace psl1 {
 
 constexpr int NT = 256;          // threads per CTA of the step kernels
 constexpr int KMAX_1D = 512;     // largest 1D mode count handled by one CTA
+constexpr int MMAX_2D = 64;      // largest 2D mode count per axis (K = Mx My <= 4096)
 constexpr int TILE = 32;         // Cholesky block size (one warp per panel)
 constexpr int INNER_CHOL = 0;    // FP32 inner solver of the refinement: blocked Cholesky
 constexpr int INNER_PCG = 1;     //                                      Jacobi-preconditioned CG
@@ -25,8 +26,8 @@ __host__ __device__ constexpr int bp_elems(int nb, int ldb) { return nb * (nb + 
 
 struct InstDev {
     int dim, K, Kp, nb;          // modes, padded to a multiple of TILE, blocks
-    int Mx, My, Q, Qh;           // Qh = Q/2 mirror pairs (1D)
-    int N, m, P, tab;
+    int Mx, My, Q, Qh;           // x axis: Q nodes, Qh = Q/2 mirror pairs
+    int N, m, P, tab;            // tab: x-axis table set
     double alpha, T, dT, dt;
     double mu, muT, ma;          // dt^a G(2-a), dT^a G(2-a), m^-a
     double cA;                   // pi^2 / L^3 : A_kl = cA k l (g_|k-l| + g_k+l)
@@ -39,6 +40,7 @@ struct InstDev {
     long long oB;                // offset in the weight pool
     long long oW;                // offset in N*K fine-history pools (uniform solver)
     int Nb;                      // b(j) table length - 1 (max of N, P, m)
+    int Qy, Qhy, tabY;           // y axis (2D): nodes, mirror pairs, table set
     int pad_;
 };
 
@@ -51,6 +53,10 @@ struct TabDev {
     long long oS;    // Qh x Mx : phi_k(x_q)      (row q, coalesced over k)
     long long oC;    // Qh x (2Mx+1) : cos(s pi (x_q - lo)/L)
     long long oStd, oSd, oCd;   // the same three tables as double-float pairs
+    long long oDt;   // Mx x Qh : phi_k'(x_q)    (row k)
+    long long oDtd;  // the same as double-float pairs
+    long long oSt32, oDt32;   // Mx x Qh FP32 copies of St and Dt (two floats per slot)
+    long long oAux2; // 2*Qh: cos(2 pi x) at x_q and at the mirror node
 };
 
 // Device error word: the first failure wins.  code < 0 is a psl1_status.

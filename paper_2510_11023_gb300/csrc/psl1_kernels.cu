@@ -1,4 +1,4 @@
-// psl1_kernels.cu -- the parareal / serial solver kernels of the 1D path.
+// psl1_kernels.cu -- the parareal / serial solver kernels (1D and 2D instantiations).
 //
 //   k_fstage        F stage: every active (instance, slice) unit runs its m
 //                   fine steps (Eq. NumericalSchemeFine); persistent CTAs pull
@@ -13,6 +13,7 @@
 #include "psl1_kernels.h"
 #include "psl1_step.cuh"
 #include "psl1_step_mixed.cuh"
+#include "psl1_step2d.cuh"
 
 namespace psl1 {
 
@@ -23,6 +24,7 @@ struct Carve {
     PcgSmem cg;
     float* fac;
     df *mz, *mh0, *mh1;      // learned-correction features and hidden activations (double-float)
+    Step2D s2;               // 2D working arrays
 };
 
 template <typename T>
@@ -31,8 +33,47 @@ __device__ __forceinline__ T* at(char* base, int off)
     return off >= 0 ? reinterpret_cast<T*>(base + off) : nullptr;
 }
 
+__device__ __forceinline__ Carve carve2d(const PathArgs& a, char* base)
+{
+    const Layout2D& L = a.L2;
+    char* gbase = reinterpret_cast<char*>(a.work + (size_t)blockIdx.x * a.work_stride);
+    auto at2 = [&](int r) -> void* {
+        if (L.off[r] < 0) return nullptr;
+        return (L.glob[r] ? gbase : base) + L.off[r];
+    };
+    Carve c{};
+    c.cur = static_cast<double*>(at2(R2_CUR));
+    c.hist = static_cast<double*>(at2(R2_HIST));
+    c.nxt = static_cast<double*>(at2(R2_NXT));
+    c.F = static_cast<double*>(at2(R2_F));
+    c.s.bad = static_cast<int*>(at2(R2_BAD));
+    c.ms.flag = c.s.bad;
+    c.s2.cdf = static_cast<df*>(at2(R2_CDF));
+    c.s2.T1 = at2(R2_T1);
+    c.s2.T2 = at2(R2_T2);
+    c.s2.N1 = at2(R2_N1);
+    c.s2.N2 = at2(R2_N2);
+    c.s2.wd = at2(R2_WD);
+    c.s2.wd32 = static_cast<float*>(at2(R2_WD32));
+    c.s2.dinv = at2(R2_DINV);
+    c.s2.x = at2(R2_PX);
+    c.s2.r = at2(R2_PR);
+    c.s2.p = at2(R2_PP);
+    c.s2.q = at2(R2_PQ);
+    c.s2.xr = static_cast<double*>(at2(R2_XR));
+    c.s2.rhs = static_cast<double*>(at2(R2_RHS));
+    c.s2.z = static_cast<float*>(at2(R2_Z));
+    c.s2.tab32 = static_cast<float*>(at2(R2_TAB32));
+    c.s2.red = at2(R2_RED);
+    return c;
+}
+
+// D2: the kernel is the 2D instantiation (1D and 2D code are compiled into
+// separate kernels so that neither inflates the other's register allocation)
+template <bool D2>
 __device__ __forceinline__ Carve carve(const PathArgs& a, char* base)
 {
+    if constexpr (D2) return carve2d(a, base);
     const SmemLayout& L = a.L;
     Carve c;
     c.cur = at<double>(base, L.cur);
@@ -139,8 +180,58 @@ SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int 
 
 size_t step_smem_bytes(const PathArgs& a) { return (size_t)a.L.total; }
 
+Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long ntab, int max_smem)
+{
+    Layout2D L;
+    const bool f64 = prec == 0;
+    const long long e = f64 ? 8 : 4;   // CG vector element
+    long long bytes[R2_COUNT];
+    bytes[R2_BAD] = 16;
+    bytes[R2_RED] = 8 * 2 * (NT / 32);
+    bytes[R2_DINV] = e * Kmax;
+    bytes[R2_PX] = e * Kmax;
+    bytes[R2_PR] = e * Kmax;
+    bytes[R2_PP] = e * Kmax;
+    bytes[R2_PQ] = e * Kmax;
+    bytes[R2_TAB32] = f64 ? 0 : 4 * 2 * ntab;
+    bytes[R2_T1] = 8 * nT;
+    bytes[R2_T2] = 8 * nT;
+    bytes[R2_Z] = f64 ? 0 : 4LL * Kmax;
+    bytes[R2_WD32] = f64 ? 0 : 4 * nN;
+    bytes[R2_N1] = 8 * nN;
+    bytes[R2_N2] = 8 * nN;
+    bytes[R2_CDF] = f64 ? 0 : 8LL * Kmax;
+    bytes[R2_XR] = f64 ? 0 : 8LL * Kmax;
+    bytes[R2_RHS] = f64 ? 0 : 8LL * Kmax;
+    bytes[R2_CUR] = 8LL * Kmax;
+    bytes[R2_HIST] = 8LL * Kmax;
+    bytes[R2_NXT] = 8LL * Kmax;
+    bytes[R2_F] = 8LL * Kmax;
+    bytes[R2_WD] = 8 * nN;
+    long long soff = 0, goff = 0;
+    for (int r = 0; r < R2_COUNT; ++r) {
+        L.off[r] = -1;
+        L.glob[r] = 0;
+        if (bytes[r] <= 0) continue;
+        const long long b = (bytes[r] + 15) / 16 * 16;
+        // the flag and reduction words always sit in shared memory
+        if (soff + b <= max_smem || r == R2_BAD || r == R2_RED) {
+            L.off[r] = (int)soff;
+            soff += b;
+        } else {
+            L.off[r] = (int)goff;
+            L.glob[r] = 1;
+            goff += b;
+        }
+    }
+    L.smem = (int)soff;
+    L.gbytes = goff;
+    return L;
+}
+
 enum { WHERE_FINE = 1, WHERE_COARSE = 2, WHERE_UNI = 3, WHERE_ONE = 4 };
 
+template <bool D2>
 __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, const double* c,
                                        const double* hist, double te, double mu, double* out, Carve& cv)
 {
@@ -150,27 +241,46 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
         cv.s.bad[1] = 0;
         cv.s.bad[2] = 0;
     }
-    if (a.prec == 0) {
-        BPack<double, TILE> A{a.work + (size_t)blockIdx.x * a.work_stride};
-        bad = step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
-    } else {
-        BPack<float, MIX_LDB> A{cv.fac};
-        bad = step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s, cv.ms, cv.cg, a.prec == 2, a.inner);
-    }
-    // algorithmic FLOPs of the step: transforms (u, moments, load: 4 K^2 multiply-adds with
-    // Q = 2K nodes), coefficient evaluation (~30 per node), and the solve -- FP64: Cholesky
-    // K^3/3 + two triangular solves 2 K^2; FP32 pipes: 4 K^2 per Toeplitz+Hankel product
-    // (refinement residuals and PCG iterations).
-    if (threadIdx.x == 0 && a.flops) {
-        const double K = I.K, K2 = K * K;
-        double f = 8.0 * K2 + 30.0 * I.Q;
+    if constexpr (D2) {
+        const TabDev& TY = a.tab[I.tabY];
         if (a.prec == 0)
-            f += K * K2 / 3.0 + 2.0 * K2;
+            bad = step2d_fp64(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad);
         else
-            f += 4.0 * K2 * (cv.s.bad[1] + cv.s.bad[2]) + (a.inner == INNER_CHOL ? K * K2 / 3.0 : 0.0);
-        atomicAdd(a.flops + a.flop_slot, f);
+            bad = step2d_mixed(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad, a.prec == 2);
+        // algorithmic FLOPs: each operator application is four folded one-axis
+        // transforms, 4 (Mx My Qy/2 + Mx Qy Qx/2) multiply-adds; the set-up
+        // (node values, load, diagonal) costs one application, the coefficient
+        // evaluation ~30 per node.
+        if (threadIdx.x == 0 && a.flops) {
+            const double ap = 8.0 * ((double)I.Mx * I.My * I.Qhy + (double)I.Mx * I.Qy * I.Qh);
+            const double f = ap * (1.0 + cv.s.bad[1] + cv.s.bad[2]) + 30.0 * I.Q * I.Qy;
+            atomicAdd(a.flops + a.flop_slot, f);
+        }
+        return bad;
+    } else {
+        if (a.prec == 0) {
+            BPack<double, TILE> A{a.work + (size_t)blockIdx.x * a.work_stride};
+            bad = step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
+        } else {
+            BPack<float, MIX_LDB> A{cv.fac};
+            bad = step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s, cv.ms, cv.cg, a.prec == 2,
+                             a.inner);
+        }
+        // algorithmic FLOPs of the step: transforms (u, moments, load: 4 K^2 multiply-adds with
+        // Q = 2K nodes), coefficient evaluation (~30 per node), and the solve -- FP64: Cholesky
+        // K^3/3 + two triangular solves 2 K^2; FP32 pipes: 4 K^2 per Toeplitz+Hankel product
+        // (refinement residuals and PCG iterations).
+        if (threadIdx.x == 0 && a.flops) {
+            const double K = I.K, K2 = K * K;
+            double f = 8.0 * K2 + 30.0 * I.Q;
+            if (a.prec == 0)
+                f += K * K2 / 3.0 + 2.0 * K2;
+            else
+                f += 4.0 * K2 * (cv.s.bad[1] + cv.s.bad[2]) + (a.inner == INNER_CHOL ? K * K2 / 3.0 : 0.0);
+            atomicAdd(a.flops + a.flop_slot, f);
+        }
+        return bad;
     }
-    return bad;
 }
 
 __device__ __forceinline__ void check_finite(const PathArgs& a, const double* v, int K, int ii, int where,
@@ -183,6 +293,7 @@ __device__ __forceinline__ void check_finite(const PathArgs& a, const double* v,
 // F_n of instance ii on coarse states U (rows 0..n, global): m fine steps with
 // the local fine history kept in the CTA's ring and the coarse history
 // m^-a sum_{i=1}^n b(n-i+r/m) (U_i - U_{i-1})  (Eq. L1Fine, difference form).
+template <bool D2>
 __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, double* Vout, double* out,
                            Carve& cv, double* ring)
 {
@@ -206,7 +317,7 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
         }
         if (tid == 0 && a.flops) atomicAdd(a.flops + a.flop_slot, 2.0 * K * (r - 1 + n));
         __syncthreads();
-        int bad = do_step(a, I, cv.cur, cv.hist, I.dT * n + I.dt * (r - 1), I.mu, cv.nxt, cv);
+        int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n + I.dt * (r - 1), I.mu, cv.nxt, cv);
         if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_FINE, n * m + r);
         check_finite(a, cv.nxt, K, ii, WHERE_FINE, n * m + r);
         for (int k = tid; k < K; k += NT) {
@@ -274,6 +385,7 @@ __device__ void learned_correction(const PathArgs& a, const InstDev& I, int n, C
 
 // G_n of instance ii on U (rows 0..n, global) -> cv.nxt.  History in the
 // difference form U_n - sum_{j=0}^{n-1} b_{n-j} (U_{j+1} - U_j) of Eq. L1Scheme.
+template <bool D2>
 __device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, Carve& cv)
 {
     const InstDev& I = a.inst[ii];
@@ -287,10 +399,11 @@ __device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, C
     }
     if (tid == 0 && a.flops) atomicAdd(a.flops + a.flop_slot, 2.0 * K * n);
     __syncthreads();
-    int bad = do_step(a, I, cv.cur, cv.hist, I.dT * n, I.muT, cv.nxt, cv);
+    int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n, I.muT, cv.nxt, cv);
     if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_COARSE, n);
     check_finite(a, cv.nxt, K, ii, WHERE_COARSE, n);
-    if (a.mlp.on) learned_correction(a, I, n, cv);
+    if constexpr (!D2)   // the learned correction is defined for 1D instances
+        if (a.mlp.on) learned_correction(a, I, n, cv);
 }
 
 // Training samples from a parareal iterate: for every (instance, n >= nfirst):
@@ -302,7 +415,7 @@ __global__ void __launch_bounds__(NT) k_iterate_dataset(PathArgs a, const double
                                                         long long base)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Carve cv = carve(a, smem_raw);
+    Carve cv = carve<false>(a, smem_raw);
     const MlpDev& M = a.mlp;
     const int ii = blockIdx.y, n = blockIdx.x;
     const InstDev& I = a.inst[ii];
@@ -343,7 +456,7 @@ __global__ void __launch_bounds__(NT) k_coarse_dataset(PathArgs a, const double*
                                                        int* counter, float* Z, float* R)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Carve cv = carve(a, smem_raw);
+    Carve cv = carve<false>(a, smem_raw);
     __shared__ int s_u;
     const MlpDev& M = a.mlp;
     for (;;) {
@@ -357,7 +470,7 @@ __global__ void __launch_bounds__(NT) k_coarse_dataset(PathArgs a, const double*
         const double* U = Us + I.oU;
         PathArgs plain = a;
         plain.mlp.on = 0;
-        coarse_step(plain, ii, n, U, cv);
+        coarse_step<false>(plain, ii, n, U, cv);
         const long long s = (long long)ii * I.P + n;
         learned_features(M, I, n, cv, Z + s * M.nin);
         for (int k = threadIdx.x; k < M.nout; k += NT)
@@ -365,11 +478,12 @@ __global__ void __launch_bounds__(NT) k_coarse_dataset(PathArgs a, const double*
     }
 }
 
+template <bool D2>
 __global__ void __launch_bounds__(NT) k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units,
                                                int nunits, int* counter, const int* nfirst, const int* active)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Carve cv = carve(a, smem_raw);
+    Carve cv = carve<D2>(a, smem_raw);
     __shared__ int s_u;
     double* ring = a.ring + (size_t)blockIdx.x * a.ring_stride;
     for (;;) {
@@ -381,16 +495,17 @@ __global__ void __launch_bounds__(NT) k_fstage(PathArgs a, const double* Uold, d
         const int ii = units[u].x, n = units[u].y;
         if (!active[ii] || n < nfirst[ii]) continue;
         const InstDev& I = a.inst[ii];
-        fine_slice(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring);
+        fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring);
     }
 }
 
+template <bool D2>
 __global__ void __launch_bounds__(NT) k_coarse_sweep(PathArgs a, const double* u0, const double* Uold,
                                                      double* Unew, const double* Fv, double* Gold, int init,
                                                      const int* nfirst, const int* active, double* incr)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Carve cv = carve(a, smem_raw);
+    Carve cv = carve<D2>(a, smem_raw);
     __shared__ double red[NT / 32];
     __shared__ double s_num, s_den;
     const int ii = blockIdx.x, tid = threadIdx.x;
@@ -412,7 +527,7 @@ __global__ void __launch_bounds__(NT) k_coarse_sweep(PathArgs a, const double* u
     double* Go = Gold + I.oPK;
     const double* Fo = Fv + I.oPK;
     for (int n = n0; n < P; ++n) {
-        coarse_step(a, ii, n, U, cv);
+        coarse_step<D2>(a, ii, n, U, cv);
         for (int k = tid; k < K; k += NT) {
             double g = cv.nxt[k];
             size_t e = (size_t)n * K + k;
@@ -460,17 +575,18 @@ __global__ void __launch_bounds__(NT) k_coarse_sweep(PathArgs a, const double* u
     if (tid == 0) incr[ii] = s_den > 0.0 ? s_num / s_den : s_num;
 }
 
+template <bool D2>
 __global__ void __launch_bounds__(NT) k_serial_hyb(PathArgs a, const double* u0, double* Us)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Carve cv = carve(a, smem_raw);
+    Carve cv = carve<D2>(a, smem_raw);
     const int ii = blockIdx.x;
     const InstDev& I = a.inst[ii];
     double* U = Us + I.oU;
     double* ring = a.ring + (size_t)blockIdx.x * a.ring_stride;
     for (int k = threadIdx.x; k < I.K; k += NT) U[k] = u0[I.oK + k];
     __syncthreads();
-    for (int n = 0; n < I.P; ++n) fine_slice(a, ii, n, U, nullptr, U + (size_t)(n + 1) * I.K, cv, ring);
+    for (int n = 0; n < I.P; ++n) fine_slice<D2>(a, ii, n, U, nullptr, U + (size_t)(n + 1) * I.K, cv, ring);
 }
 
 __global__ void k_uni_init(const InstDev* inst, const double* u0, double* Wcur, double* Us)
@@ -504,11 +620,12 @@ __global__ void __launch_bounds__(NT) k_uni_hist(const InstDev* inst, const doub
     }
 }
 
+template <bool D2>
 __global__ void __launch_bounds__(NT) k_uni_step(PathArgs a, double* Wcur, double* dW, double* Us, int j,
                                                  const double* part, int chunk, int maxchunks)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Carve cv = carve(a, smem_raw);
+    Carve cv = carve<D2>(a, smem_raw);
     const int ii = blockIdx.x, tid = threadIdx.x;
     const InstDev& I = a.inst[ii];
     if (j >= I.N) return;
@@ -521,7 +638,7 @@ __global__ void __launch_bounds__(NT) k_uni_step(PathArgs a, double* Wcur, doubl
         cv.hist[k] = h;
     }
     __syncthreads();
-    int bad = do_step(a, I, cv.cur, cv.hist, I.dt * j, I.mu, cv.nxt, cv);
+    int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dt * j, I.mu, cv.nxt, cv);
     if (bad >= 0 && tid == 0) report(a.status, -2, ii, WHERE_UNI, j);
     check_finite(a, cv.nxt, K, ii, WHERE_UNI, j);
     const bool node = ((j + 1) % I.m) == 0;
@@ -533,37 +650,40 @@ __global__ void __launch_bounds__(NT) k_uni_step(PathArgs a, double* Wcur, doubl
     }
 }
 
+template <bool D2>
 __global__ void __launch_bounds__(NT) k_one_step(PathArgs a, int ii, const double* c, const double* hist,
                                                  double te, double mu, double* out)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Carve cv = carve(a, smem_raw);
+    Carve cv = carve<D2>(a, smem_raw);
     const InstDev& I = a.inst[ii];
     for (int k = threadIdx.x; k < I.K; k += NT) {
         cv.cur[k] = c[k];
         cv.hist[k] = hist[k];
     }
     __syncthreads();
-    int bad = do_step(a, I, cv.cur, cv.hist, te, mu, cv.nxt, cv);
+    int bad = do_step<D2>(a, I, cv.cur, cv.hist, te, mu, cv.nxt, cv);
     if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_ONE, bad);
     check_finite(a, cv.nxt, I.K, ii, WHERE_ONE, 0);
     for (int k = threadIdx.x; k < I.K; k += NT) out[k] = cv.nxt[k];
 }
 
+template <bool D2>
 __global__ void __launch_bounds__(NT) k_one_slice(PathArgs a, int ii, int n, const double* U, double* V)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Carve cv = carve(a, smem_raw);
+    Carve cv = carve<D2>(a, smem_raw);
     const InstDev& I = a.inst[ii];
-    fine_slice(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring);
+    fine_slice<D2>(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring);
 }
 
+template <bool D2>
 __global__ void __launch_bounds__(NT) k_one_coarse(PathArgs a, int ii, int n, const double* U, double* out)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Carve cv = carve(a, smem_raw);
+    Carve cv = carve<D2>(a, smem_raw);
     const InstDev& I = a.inst[ii];
-    coarse_step(a, ii, n, U, cv);
+    coarse_step<D2>(a, ii, n, U, cv);
     for (int k = threadIdx.x; k < I.K; k += NT) out[k] = cv.nxt[k];
 }
 
@@ -573,6 +693,20 @@ static PathArgs slot(const PathArgs& a, int s)
     b.flop_slot = s;
     return b;
 }
+
+template <typename... KA, typename... Args>
+static cudaError_t launch_k(void (*k)(KA...), dim3 grid, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NT, smem, s>>>(args...);
+    return cudaGetLastError();
+}
+
+// the 1D or the 2D instantiation of a step kernel
+#define LAUNCH_STEP_KERNEL(kern, grid, smem, s, ...)                              \
+    (a.dim2 ? launch_k(kern<true>, grid, smem, s, __VA_ARGS__)                    \
+            : launch_k(kern<false>, grid, smem, s, __VA_ARGS__))
 
 // ------------------------------------------------------------------ allocation-free slice
 // For callers that must not allocate device memory while they run (a real-time
@@ -585,12 +719,13 @@ static PathArgs slot(const PathArgs& a, int s)
 // array, so calls that overlap on the GPU race.
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
+template <bool D2>
 __global__ void __launch_bounds__(NT) k_one_slice_noalloc(PathArgs a, int ii, int n, const double* U, double* V)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Carve cv = carve(a, smem_raw);
+    Carve cv = carve<D2>(a, smem_raw);
     const InstDev& I = a.inst[ii];
-    fine_slice(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring);
+    fine_slice<D2>(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring);
 }
 
 namespace {
@@ -618,28 +753,18 @@ cudaError_t launch_one_slice_noalloc(const PathArgs& a, int b, int n, const doub
     a2.work_stride = work_doubles;
     a2.nslots = 1;
     size_t sm = step_smem_bytes(a2);
-    e = cudaFuncSetAttribute(k_one_slice_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_one_slice_noalloc<<<1, NT, sm, s>>>(a2, b, n, U, V);
-    return cudaGetLastError();
+    return a.dim2 ? launch_k(k_one_slice_noalloc<true>, 1, sm, s, a2, b, n, U, V)
+                  : launch_k(k_one_slice_noalloc<false>, 1, sm, s, a2, b, n, U, V);
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename Kern>
-static cudaError_t prep(Kern k, size_t smem)
-{
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
 cudaError_t launch_fstage(const PathArgs& a, const double* Uold, double* Fv, const int2* units, int nunits,
                           int* counter, const int* nfirst, const int* active, int grid, cudaStream_t s)
 {
     size_t sm = step_smem_bytes(a);
-    cudaError_t e = prep(k_fstage, sm);
-    if (e != cudaSuccess) return e;
     if (grid > a.nslots) grid = a.nslots;
-    k_fstage<<<grid, NT, sm, s>>>(slot(a, 0), Uold, Fv, units, nunits, counter, nfirst, active);
-    return cudaGetLastError();
+    return LAUNCH_STEP_KERNEL(k_fstage, grid, sm, s, slot(a, 0), Uold, Fv, units, nunits, counter, nfirst,
+                              active);
 }
 
 cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, const double* Uold, double* Unew,
@@ -647,19 +772,14 @@ cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, cons
                                 const int* active, double* incr, cudaStream_t s)
 {
     size_t sm = step_smem_bytes(a);
-    cudaError_t e = prep(k_coarse_sweep, sm);
-    if (e != cudaSuccess) return e;
-    k_coarse_sweep<<<B, NT, sm, s>>>(slot(a, 1), u0, Uold, Unew, Fv, Gold, init, nfirst, active, incr);
-    return cudaGetLastError();
+    return LAUNCH_STEP_KERNEL(k_coarse_sweep, B, sm, s, slot(a, 1), u0, Uold, Unew, Fv, Gold, init, nfirst,
+                              active, incr);
 }
 
 cudaError_t launch_serial_hyb(const PathArgs& a, int B, const double* u0, double* Us, cudaStream_t s)
 {
     size_t sm = step_smem_bytes(a);
-    cudaError_t e = prep(k_serial_hyb, sm);
-    if (e != cudaSuccess) return e;
-    k_serial_hyb<<<B, NT, sm, s>>>(slot(a, 2), u0, Us);
-    return cudaGetLastError();
+    return LAUNCH_STEP_KERNEL(k_serial_hyb, B, sm, s, slot(a, 2), u0, Us);
 }
 
 cudaError_t launch_uni_init(const PathArgs& a, int B, const double* u0, double* Wcur, double* Us, cudaStream_t s)
@@ -682,49 +802,34 @@ cudaError_t launch_uni_step(const PathArgs& a, int B, double* Wcur, double* dW, 
                             const double* part, int chunk, int maxchunks, cudaStream_t s)
 {
     size_t sm = step_smem_bytes(a);
-    cudaError_t e = prep(k_uni_step, sm);
-    if (e != cudaSuccess) return e;
-    k_uni_step<<<B, NT, sm, s>>>(slot(a, 2), Wcur, dW, Us, j, part, chunk, maxchunks);
-    return cudaGetLastError();
+    return LAUNCH_STEP_KERNEL(k_uni_step, B, sm, s, slot(a, 2), Wcur, dW, Us, j, part, chunk, maxchunks);
 }
 
 cudaError_t launch_one_step(const PathArgs& a, int b, const double* c, const double* hist, double te, double mu,
                             double* out, cudaStream_t s)
 {
     size_t sm = step_smem_bytes(a);
-    cudaError_t e = prep(k_one_step, sm);
-    if (e != cudaSuccess) return e;
-    k_one_step<<<1, NT, sm, s>>>(slot(a, 3), b, c, hist, te, mu, out);
-    return cudaGetLastError();
+    return LAUNCH_STEP_KERNEL(k_one_step, 1, sm, s, slot(a, 3), b, c, hist, te, mu, out);
 }
 
 cudaError_t launch_one_slice(const PathArgs& a, int b, int n, const double* U, double* V, cudaStream_t s)
 {
     size_t sm = step_smem_bytes(a);
-    cudaError_t e = prep(k_one_slice, sm);
-    if (e != cudaSuccess) return e;
-    k_one_slice<<<1, NT, sm, s>>>(slot(a, 3), b, n, U, V);
-    return cudaGetLastError();
+    return LAUNCH_STEP_KERNEL(k_one_slice, 1, sm, s, slot(a, 3), b, n, U, V);
 }
 
 cudaError_t launch_coarse_dataset(const PathArgs& a, const double* Us, const int2* units, int nunits, int* counter,
                                   float* Z, float* R, int grid, cudaStream_t s)
 {
     size_t sm = step_smem_bytes(a);
-    cudaError_t e = prep(k_coarse_dataset, sm);
-    if (e != cudaSuccess) return e;
     if (grid > a.nslots) grid = a.nslots;
-    k_coarse_dataset<<<grid, NT, sm, s>>>(slot(a, 3), Us, units, nunits, counter, Z, R);
-    return cudaGetLastError();
+    return launch_k(k_coarse_dataset, grid, sm, s, slot(a, 3), Us, units, nunits, counter, Z, R);
 }
 
 cudaError_t launch_one_coarse(const PathArgs& a, int b, int n, const double* U, double* out, cudaStream_t s)
 {
     size_t sm = step_smem_bytes(a);
-    cudaError_t e = prep(k_one_coarse, sm);
-    if (e != cudaSuccess) return e;
-    k_one_coarse<<<1, NT, sm, s>>>(slot(a, 3), b, n, U, out);
-    return cudaGetLastError();
+    return LAUNCH_STEP_KERNEL(k_one_coarse, 1, sm, s, slot(a, 3), b, n, U, out);
 }
 
 }  // namespace psl1

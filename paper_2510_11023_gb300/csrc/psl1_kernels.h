@@ -12,6 +12,7 @@ struct TableJob {
     double lo, hi;
     double *xh, *wh, *St, *S, *C, *aux;
     double *Std, *Sd, *Cd;   // double-float copies (float pairs stored in 8-byte slots)
+    double *Dt, *Dtd, *St32, *Dt32, *aux2;   // derivative table, FP32 copies, cos(2 pi x)
 };
 
 // Byte offsets of the per-CTA shared-memory regions (host-computed; -1 = absent).
@@ -22,6 +23,23 @@ struct SmemLayout {
     int mz, mh0, mh1;                                            // learned correction inference
     int total;
 };
+
+// 2D working arrays: each region lives in shared memory when it fits (in the
+// order listed: most used first), else in the CTA slot's global workspace.
+enum Region2D {
+    R2_BAD, R2_RED, R2_DINV, R2_PX, R2_PR, R2_PP, R2_PQ, R2_TAB32, R2_T1, R2_T2, R2_Z, R2_WD32,
+    R2_N1, R2_N2, R2_CDF, R2_XR, R2_RHS, R2_CUR, R2_HIST, R2_NXT, R2_F, R2_WD, R2_COUNT
+};
+
+struct Layout2D {
+    int off[R2_COUNT];               // byte offset (shared memory or slot workspace); -1: absent
+    unsigned char glob[R2_COUNT];    // 1: in the slot's global workspace
+    int smem;                        // shared-memory bytes per CTA
+    long long gbytes;                // global workspace bytes per slot
+};
+
+// Kmax: modes; nT: max Mx (Qy + 1); nN: max Qx Qy; ntab: max Mx Qx/2 + My Qy/2.
+Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long ntab, int max_smem);
 
 // Pointers and sizes every solver kernel needs.
 struct PathArgs {
@@ -43,6 +61,8 @@ struct PathArgs {
     double* flops;           // algorithmic FLOP accumulators (by slot), may be null
     int flop_slot;           // 0 F stage, 1 coarse sweeps, 2 serial solvers, 3 single pieces
     MlpDev mlp;              // learned coarse correction (mlp.on = 0: plain L1 G)
+    int dim2;                // 2D instances (the 2D layout below applies)
+    Layout2D L2;
 };
 
 SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem);

@@ -44,10 +44,12 @@ __global__ void k_gauss_legendre_half(int Q, double lo, double hi, double* xh, d
 }
 
 // Basis tables for one (Mx, Qx, box): St[k][q], S[q][k] = sqrt(2/L) sin(k pi th_q),
-// C[q][s] = cos(s pi th_q), th_q = (x_q - lo)/L, and the node functions of the
-// coefficient families at x_q and its mirror.
+// C[q][s] = cos(s pi th_q), Dt[k][q] = sqrt(2/L) (k pi/L) cos(k pi th_q) (the
+// derivative), th_q = (x_q - lo)/L, and the node functions of the coefficient
+// families at x_q and its mirror.
 __global__ void k_basis_tables(int Mx, int Qh, double lo, double hi, const double* xh, double* St,
-                               double* S, double* C, double* aux, df* Std, df* Sd, df* Cd)
+                               double* S, double* C, double* aux, df* Std, df* Sd, df* Cd, double* Dt,
+                               df* Dtd, float* St32, float* Dt32, double* aux2)
 {
     int q = blockIdx.x;
     if (q >= Qh) return;
@@ -56,10 +58,15 @@ __global__ void k_basis_tables(int Mx, int Qh, double lo, double hi, const doubl
     double sc = sqrt(2.0 / L);
     for (int k = threadIdx.x + 1; k <= Mx; k += blockDim.x) {
         double v = sc * sinpi(k * th);
+        double dv = sc * (k * 3.141592653589793 / L) * cospi(k * th);   // phi_k'(x_q)
         St[(size_t)(k - 1) * Qh + q] = v;
         S[(size_t)q * Mx + (k - 1)] = v;
         Std[(size_t)(k - 1) * Qh + q] = df_from_double(v);
         Sd[(size_t)q * Mx + (k - 1)] = df_from_double(v);
+        Dt[(size_t)(k - 1) * Qh + q] = dv;
+        Dtd[(size_t)(k - 1) * Qh + q] = df_from_double(dv);
+        St32[(size_t)(k - 1) * Qh + q] = (float)v;
+        Dt32[(size_t)(k - 1) * Qh + q] = (float)dv;
     }
     for (int s = threadIdx.x; s <= 2 * Mx; s += blockDim.x) {
         double v = cospi(s * th);
@@ -72,6 +79,8 @@ __global__ void k_basis_tables(int Mx, int Qh, double lo, double hi, const doubl
         aux[4 * q + 1] = sinpi(2.0 * xa);
         aux[4 * q + 2] = sinpi(xb);
         aux[4 * q + 3] = sinpi(2.0 * xb);
+        aux2[2 * q + 0] = cospi(2.0 * xa);
+        aux2[2 * q + 1] = cospi(2.0 * xb);
     }
 }
 
@@ -112,7 +121,9 @@ cudaError_t launch_tables(const TableJob& job, cudaStream_t s)
     k_gauss_legendre_half<<<(Q + 127) / 128, 128, 0, s>>>(Q, job.lo, job.hi, job.xh, job.wh);
     k_basis_tables<<<job.Qh, 128, 0, s>>>(job.Mx, job.Qh, job.lo, job.hi, job.xh, job.St, job.S, job.C,
                                           job.aux, reinterpret_cast<df*>(job.Std), reinterpret_cast<df*>(job.Sd),
-                                          reinterpret_cast<df*>(job.Cd));
+                                          reinterpret_cast<df*>(job.Cd), job.Dt, reinterpret_cast<df*>(job.Dtd),
+                                          reinterpret_cast<float*>(job.St32), reinterpret_cast<float*>(job.Dt32),
+                                          job.aux2);
     return cudaGetLastError();
 }
 

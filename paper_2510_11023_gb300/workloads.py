@@ -130,6 +130,55 @@ def e1(K: int = 16, P: int = 256, m: int = 32, alpha: float = 0.5) -> Workload:
     return Workload("paper E1 shape K=%d P=%d m=%d" % (K, P, m), P, [spec], [u0])
 
 
+def _u0_2d(rng, Mx: int, My: int) -> np.ndarray:
+    """c_kl = z_kl / (k^2 + l^2), z ~ N(0, 1), row-major with the y mode fastest."""
+    k = np.arange(1, Mx + 1, dtype=np.float64)[:, None]
+    l = np.arange(1, My + 1, dtype=np.float64)[None, :]
+    return (rng.standard_normal((Mx, My)) / (k * k + l * l)).reshape(-1)
+
+
+def cfg3(M: int = 32, N: int = 2048, P: int = 128, alpha: float = 0.4, seed: int = 20251012) -> Workload:
+    """2D, one instance: Mx = My = M modes, 2M x 2M Gauss nodes, D = 1 + 0.5/(1+u^2),
+    f = 0.05 u (1-u), u0 coefficients z / (k^2 + l^2)."""
+    rng = np.random.default_rng(seed)
+    spec = InstanceSpec(dim=2, modes=(M, M), nsteps=N, alpha=alpha, dpar=D_CFG1, fpar=(0, 0, 0.05, 0, 0, 0, 0, 0))
+    return Workload("2D M=%d x %d N=%d P=%d alpha=%g" % (M, M, N, P, alpha), P, [spec], [_u0_2d(rng, M, M)],
+                    {"seed": seed})
+
+
+def cfg5(B: int = 16, M: int = 64, N: int = 8192, P: int = 256, alpha: float = 0.6,
+         seed: int = 20251015) -> Workload:
+    """2D batched: B instances, Mx = My = M modes, 2M x 2M Gauss nodes,
+    D = 1 + 0.5/(1+u^2) (1 + 0.3 cos 2 pi y), f = 0.1 sin u, u0 coefficients z / (k^2 + l^2)."""
+    rng = np.random.default_rng(seed)
+    specs, u0 = [], []
+    for _ in range(B):
+        specs.append(InstanceSpec(dim=2, modes=(M, M), nsteps=N, alpha=alpha, dpar=(1.0, 0.5, 0, 0, 0, 0, 0, 0.3),
+                                  fpar=(0, 0.1, 0, 0, 0, 0, 0, 0)))
+        u0.append(_u0_2d(rng, M, M))
+    return Workload("2D batched B=%d M=%d x %d N=%d P=%d alpha=%g" % (B, M, M, N, P, alpha), P, specs, u0,
+                    {"seed": seed})
+
+
+def small_batch_2d(seed: int = 6, P: int = 4) -> Workload:
+    """A small ragged 2D batch for parity tests: Mx != My, odd mode counts,
+    non-default node counts, a non-unit box, y-dependent D, mixed alpha including 1."""
+    rng = np.random.default_rng(seed)
+    shapes = [((5, 7), (0, 0)), ((8, 8), (0, 0)), ((12, 9), (26, 20)), ((3, 16), (0, 0))]
+    ms = [3, 2, 4, 1]
+    al = [0.4, 1.0, 0.6, 0.3]
+    dps = [D_CFG1, (1.0, 0.5, 0, 0, 0.1, 0.2, 0, 0.3), (0.8, 0.4, 0, 0.2, 0, 0, 0.2, 0), (1.0, 0.5, 0, 0, 0, 0, 0, 0.3)]
+    fps = [(0, 0, 0.05, 0, 0, 0, 0, 0), (0, 0.1, 0, 0, 0, 0, 0, 0), F_COS, (0, 0, 0, 0.5, 0, 0, 0, 0)]
+    specs, u0 = [], []
+    for b in range(len(shapes)):
+        (mx, my), (qx, qy) = shapes[b]
+        lo, hi = ((-0.5, 0.25), (1.0, 2.0)) if b == 2 else ((0.0, 0.0), (1.0, 1.0))
+        specs.append(InstanceSpec(dim=2, modes=(mx, my), qnodes=(qx, qy), nsteps=P * ms[b], alpha=al[b], lo=lo, hi=hi,
+                                  dpar=dps[b], fpar=fps[b]))
+        u0.append(_u0_2d(rng, mx, my))
+    return Workload("small ragged 2D batch", P, specs, u0, {"seed": seed})
+
+
 def small_batch(seed: int = 5, B: int = 5, P: int = 4) -> Workload:
     """A small ragged batch for parity tests: uneven K (including K not a multiple
     of 32 and K > 32), uneven m, mixed alpha including alpha = 1."""

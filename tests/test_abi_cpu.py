@@ -45,6 +45,34 @@ def test_invalid_arguments_rejected_before_device_use():
     assert L.psl1_create(ctypes.byref(h), 1, arr, 8, 0, None) == -1
 
 
+def test_invalid_2d_arguments_rejected_before_device_use():
+    L = psl1.load()
+    h = ctypes.c_void_p()
+    wl = workloads.small_batch_2d()
+
+    def create(*insts):
+        arr = (psl1.Instance * len(insts))(*insts)
+        return L.psl1_create(ctypes.byref(h), len(insts), arr, wl.P, 0, None)
+
+    ok = psl1.to_instance(wl.specs[0])
+    bad = psl1.to_instance(wl.specs[0])
+    bad.dim = 3
+    assert create(bad) == -1
+    bad = psl1.to_instance(wl.specs[0])
+    bad.modes[1] = 65                      # more than 64 modes per axis in 2D
+    assert create(bad) == -1
+    assert b"modes[1]" in L.psl1_last_error(None)
+    bad = psl1.to_instance(wl.specs[0])
+    bad.qnodes[1] = 15                     # odd node count
+    assert create(bad) == -1
+    bad = psl1.to_instance(wl.specs[0])
+    bad.hi[1] = bad.lo[1]                  # empty y interval
+    assert create(bad) == -1
+    one_d = psl1.to_instance(workloads.cfg1(N=wl.P * 4, P=wl.P).specs[0])
+    assert create(ok, one_d) == -1        # 1D and 2D instances in one handle
+    assert b"same dim" in L.psl1_last_error(None)
+
+
 def test_no_cpu_fallback_without_gpu():
     import torch
     if torch.cuda.is_available():

@@ -1,0 +1,165 @@
+"""GPU parity of the 2D tensor-product path against the CPU oracle, through the
+C ABI: single steps (FP64 and mixed paths) over ragged shapes, boxes and
+coefficient families, the fine and coarse propagators, the serial solvers and
+parareal on a small ragged 2D batch, one full-size 32 x 32-mode step, and the
+diagonal-solve property at 64 x 64 modes.
+
+Tolerances: FP64 path 1e-10 relative (the solve is CG to a relative residual of
+1e-14); mixed path the same on solves (refinement residual in double-float,
+stopped at a correction of 1e-11 of the iterate); FP32-only path 1e-4 per step."""
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_11023_gb300 import psl1, workloads
+from helpers import oracle_prob, rel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+D_XY = (1.0, 0.5, 0, 0, 0.1, 0.2, 0, 0.3)          # (1 + 0.5/(1+u^2) X1) X0 with x- and y-terms
+F_MIX = (0.1, 0.05, 0.02, 0.3, 0, 0, 0, 0)          # cos, sin, u(1-u) and sin(pi x) e^{-t} terms
+
+SHAPES = [((1, 1), (0, 0)), ((5, 7), (0, 0)), ((8, 8), (0, 0)), ((12, 9), (26, 20)), ((3, 16), (0, 0)),
+          ((20, 17), (0, 0)), ((32, 32), (0, 0))]
+
+
+def _spec(modes, q=(0, 0), dpar=D_XY, fpar=F_MIX, lo=(0.0, 0.0), hi=(1.0, 1.0), N=8, alpha=0.5):
+    return workloads.InstanceSpec(dim=2, modes=modes, qnodes=q, nsteps=N, alpha=alpha, lo=lo, hi=hi, dpar=dpar,
+                                  fpar=fpar)
+
+
+def _coeffs(rng, Mx, My):
+    k = np.arange(1, Mx + 1)[:, None]
+    l = np.arange(1, My + 1)[None, :]
+    return (rng.standard_normal((Mx, My)) / (k * k + l * l)).reshape(-1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_single_step_2d(prec, shape):
+    spec = _spec(*shape)
+    Mx, My = spec.modes
+    rng = np.random.default_rng(Mx * 100 + My)
+    c = _coeffs(rng, Mx, My)
+    hist = c + 0.01 * _coeffs(rng, Mx, My)
+    op = oracle_prob(spec, 2)
+    with psl1.Problem([spec], 2, precision=prec) as pr:
+        for te, mu in ((0.0, 0.03), (0.37, 0.2), (0.9, 1e-4)):
+            g = pr.step(0, c, te, mu, hist)
+            o = O.step(op, c, te, mu, hist)
+            assert rel(g, o) < 1e-11, (shape, prec, te, mu, rel(g, o))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_single_step_2d_box_and_manufactured_source(prec):
+    # a non-unit box, and the manufactured source S1 (a function of x, t only)
+    cases = [_spec((10, 6), lo=(-0.5, 0.25), hi=(1.0, 2.0)),
+             _spec((9, 11), dpar=workloads.D_CFG1, fpar=(0, 0, 0, 0, 1, 0, 0, 0)),
+             _spec((7, 7), dpar=(1.0, 0, 0.3, 0.2, 0, 0.1, 0, 0), fpar=(0, 0, 0, 1.0, 0, 0, 0, 0))]
+    for spec in cases:
+        Mx, My = spec.modes
+        c = _coeffs(np.random.default_rng(7), Mx, My)
+        with psl1.Problem([spec], 2, precision=prec) as pr:
+            g = pr.step(0, c, 0.4, 0.05, c)
+        assert rel(g, O.step(oracle_prob(spec, 2), c, 0.4, 0.05, c)) < 1e-11
+
+
+def test_single_step_2d_fp32_only():
+    spec = _spec((16, 12))
+    c = _coeffs(np.random.default_rng(8), 16, 12)
+    with psl1.Problem([spec], 2, precision="fp32") as pr:
+        g = pr.step(0, c, 0.3, 0.05, c)
+    assert rel(g, O.step(oracle_prob(spec, 2), c, 0.3, 0.05, c)) < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [0, 1, 3])
+def test_fine_and_coarse_propagators_2d(prec, n):
+    wl = workloads.small_batch_2d()
+    b = 2                                       # 12 x 9 modes, 26 x 20 nodes, non-unit box
+    spec, P = wl.specs[b], wl.P
+    op = oracle_prob(spec, P)
+    U = O.coarse_sweep(op, wl.u0[b])
+    with psl1.Problem([spec], P, precision=prec) as pr:
+        V = pr.fine_slice(0, n, U[: n + 1])
+        G = pr.coarse_step(0, n, U[: n + 1])
+    assert rel(V, O.fine_slice(op, n, U[: n + 1])) < TOL
+    assert rel(G, O.coarse_step(op, n, U[: n + 1])) < TOL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_small_ragged_2d_batch_parareal_and_serial(prec):
+    wl = workloads.small_batch_2d()
+    with psl1.Problem(wl, precision=prec) as pr:
+        pr.solve_parareal(tol=1e-12)
+        its = pr.get_iterations()
+        U = pr.get_coeffs("parareal")
+        pr.solve_serial("hybrid")
+        S = pr.get_coeffs("serial")
+        pr.solve_serial("uniform")
+        W = pr.get_coeffs("serial")
+    for b, spec in enumerate(wl.specs):
+        op = oracle_prob(spec, wl.P)
+        Uo, _, ko = O.parareal(op, wl.u0[b], tol=1e-12)
+        assert abs(int(its[b]) - ko) <= (0 if prec == "fp64" else 1), (b, its[b], ko)
+        assert rel(U[b], Uo[-1]) < TOL, b
+        assert rel(S[b], O.serial_hyb(op, wl.u0[b])) < TOL, b
+        assert rel(W[b], O.serial_uni(op, wl.u0[b])[:: op.m]) < TOL, b
+
+
+def test_parareal_finite_termination_2d():
+    wl = workloads.small_batch_2d()
+    spec, u0 = wl.specs[0], wl.u0[0]
+    with psl1.Problem([spec], wl.P) as pr:
+        pr.set_u0(u0)
+        pr.keep_iterates(True)
+        k = pr.solve_parareal(tol=0.0)
+        assert k == wl.P
+        pr.solve_serial("hybrid")
+        S = pr.get_coeffs("serial")[0]
+        for j in range(k + 1):
+            Uj = pr.get_iterate(j)[0]
+            assert np.abs(Uj[: j + 1] - S[: j + 1]).max() <= 1e-13 * np.abs(S).max(), j
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_step_32x32_modes(prec):
+    # one L1 step at the 32 x 32-mode, 64 x 64-node size of the 2D single-instance
+    # workload against the oracle's stored result (tests/golden/make_step2d_32x32.py)
+    sys.path.insert(0, GOLDEN)
+    from make_step2d_32x32 import inputs
+    spec, P, c, hist, te, mu = inputs()
+    ref = np.loadtxt(os.path.join(GOLDEN, "step2d_32x32.txt"))
+    with psl1.Problem([spec], P, precision=prec) as pr:
+        g = pr.step(0, c, te, mu, hist)
+    assert rel(g, ref) < 1e-11, rel(g, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_diagonal_property_64x64_modes(prec):
+    # D = 1, f = 0 at 64 x 64 modes and 128 x 128 nodes: the step is the diagonal
+    # solve hist_kl / (1 + mu pi^2 (k^2 + l^2)) (quadrature exact to ~1e-13 here)
+    spec = _spec((64, 64), dpar=(1.0, 0, 0, 0, 0, 0, 0, 0), fpar=(0,) * 8, N=8192)
+    rng = np.random.default_rng(10)
+    c = _coeffs(rng, 64, 64)
+    hist = c + 0.1 * _coeffs(rng, 64, 64)
+    k = np.repeat(np.arange(1, 65), 64)
+    l = np.tile(np.arange(1, 65), 64)
+    for mu in (0.02, 0.6):
+        ref = hist / (1 + mu * math.pi**2 * (k**2 + l**2))
+        with psl1.Problem([spec], 256, precision=prec) as pr:
+            g = pr.step(0, c, 0.5, mu, hist)
+        assert rel(g, ref) < 1e-11, (prec, mu, rel(g, ref))
+
+
+def test_learned_correction_rejected_for_2d():
+    wl = workloads.small_batch_2d()
+    with psl1.Problem(wl) as pr, psl1.MLP(nU=16, nH=8, width=32, nout=16) as m:
+        with pytest.raises(psl1.PSL1Error) as ei:
+            pr.set_coarse(m)
+        assert ei.value.status == -1

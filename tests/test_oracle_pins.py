@@ -150,6 +150,37 @@ def test_stiffness_constant_D_2d():
     assert np.abs(A - ref).max() < 1e-11 * ref.max()
 
 
+def test_step_2d_constant_D_is_a_diagonal_solve():
+    # D = d0 and f = 0 on a box (Lx, Ly): a(d0; phi_kl, phi_k'l') = d0 pi^2 (k^2/Lx^2 + l^2/Ly^2)
+    # delta, so (I + mu A) c = hist decouples mode by mode (Eq. NumericalSchemeFine)
+    Mx, My, d0, mu = 6, 5, 1.3, 0.07
+    lo, hi = (-0.5, 0.25), (1.0, 2.0)
+    p = O.make_prob(dim=2, Mx=Mx, My=My, Qx=48, Qy=48, N=4, P=1, alpha=0.5, lo=lo, hi=hi,
+                    dpar=(d0, 0, 0, 0), fpar=(0,))
+    Lx, Ly = hi[0] - lo[0], hi[1] - lo[1]
+    rng = np.random.default_rng(3)
+    hist = rng.standard_normal(Mx * My)
+    c = rng.standard_normal(Mx * My)
+    k = np.repeat(np.arange(1, Mx + 1), My)
+    l = np.tile(np.arange(1, My + 1), Mx)
+    ref = hist / (1 + mu * d0 * math.pi**2 * (k**2 / Lx**2 + l**2 / Ly**2))
+    assert np.abs(O.step(p, c, 0.3, mu, hist) - ref).max() < 1e-12
+
+
+def test_step_2d_separable_source_closed_form():
+    # f = c3 sin(pi x) e^{-t} on the unit square: F_kl = c3 e^{-t} int sin(pi x) phi_k dx int phi_l dy
+    #   = c3 e^{-t} delta_k1 (1 - (-1)^l) / (l pi);  with hist = 0 the step is mu F / (1 + mu pi^2 (k^2 + l^2))
+    Mx, My, mu, t, c3 = 4, 7, 0.05, 0.4, 0.8
+    p = O.make_prob(dim=2, Mx=Mx, My=My, Qx=40, Qy=40, N=4, P=1, alpha=0.5, dpar=(1.0, 0, 0, 0),
+                    fpar=(0, 0, 0, c3))
+    k = np.repeat(np.arange(1, Mx + 1), My)
+    l = np.tile(np.arange(1, My + 1), Mx)
+    F = np.where(k == 1, c3 * math.exp(-t) * (1 - np.cos(l * math.pi)) / (l * math.pi), 0.0)
+    ref = mu * F / (1 + mu * math.pi**2 * (k**2 + l**2))
+    got = O.step(p, np.zeros(Mx * My), t, mu, np.zeros(Mx * My))
+    assert np.abs(got - ref).max() < 1e-14
+
+
 def test_stiffness_toeplitz_hankel_identity():
     # product-to-sum: phi_k' phi_l' = k l pi^2 (cos((k-l) pi x) + cos((k+l) pi x)), so
     # A_kl = k l pi^2 (g_|k-l| + g_{k+l}), g_s = sum_q w_q D_q cos(s pi x_q) -- exact at node level
