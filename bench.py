@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "fp32"])
-    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--workload", default="batched1d", choices=["batched1d", "2d", "2d-batched"],
+                    help="batched1d: the headline 1D batch; 2d: one 32 x 32-mode instance, N = 2048, P = 128; "
+                         "2d-batched: --batch instances of 64 x 64 modes, N = 8192, P = 256")
+    ap.add_argument("--batch", type=int, default=0, help="instances (0: 256 for batched1d, 16 for 2d-batched)")
     ap.add_argument("--seed", type=int, default=20251011)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -160,11 +163,45 @@ def oracle_prob(spec, P):
                        lo=spec.lo, hi=spec.hi, dpar=spec.dpar, fpar=spec.fpar)
 
 
+def make_workload(args, rank: int = 0):
+    from paper_2510_11023_gb300 import workloads
+    if args.workload == "2d":
+        return workloads.cfg3()
+    if args.workload == "2d-batched":
+        return workloads.cfg5(B=args.batch or 16)
+    return workloads.cfg2(B=args.batch or 256, seed=args.seed + rank)
+
+
+def oracle_throughput_2d(wl, seconds: float) -> tuple:
+    """2D: one oracle step of a reduced instance (half the modes per axis,
+    same node ratio), repeated while time remains, scaled to the full size by
+    the oracle's own cost model: its stiffness sum costs K^2 Q, 64x more at
+    twice the modes per axis.  Returns (fine step-modes per second, seconds, steps)."""
+    import dataclasses
+
+    import oracle as O
+    O.build()
+    s = wl.specs[0]
+    small = dataclasses.replace(s, modes=(s.modes[0] // 2, s.modes[1] // 2))
+    op = oracle_prob(small, wl.P)
+    c = np.zeros(small.K)
+    c[0] = 0.5
+    scale = (s.K / small.K) ** 2 * (s.Q / small.Q)
+    t0, nstep = time.perf_counter(), 0
+    while nstep == 0 or time.perf_counter() - t0 < seconds:
+        O.step(op, c, 0.1, 0.01, c)
+        nstep += 1
+    dt = time.perf_counter() - t0
+    return nstep * s.K / (dt * scale), dt, nstep
+
+
 def oracle_throughput(wl, S, seconds: float) -> tuple:
     """The FP64 oracle (single thread) on a bounded sample of the workload:
     fine propagators of the middle slice of successive instances (history from
     S, or from the oracle's coarse sweep), until `seconds` of CPU time are spent."""
     import oracle as O
+    if wl.specs[0].dim == 2:
+        return oracle_throughput_2d(wl, seconds)
     O.build()
     n = wl.P // 2
     work, t0, inst = 0.0, time.perf_counter(), 0
@@ -183,7 +220,7 @@ def reference_arm(args, dist: Dist):
     from paper_2510_11023_gb300 import workloads
     if dist.rank != 0:
         return
-    wl = workloads.cfg2(B=args.batch, seed=args.seed)
+    wl = make_workload(args)
     per_step = args.ref_step_seconds or max(2.0, 120.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         oracle_throughput(wl, None, per_step / 4)
@@ -195,6 +232,9 @@ def reference_arm(args, dist: Dist):
     v = float(np.mean(vals))
     sample = (f"oracle fine propagator F_n (n = P/2, coarse-sweep history) of successive instances of the "
               f"batched workload, ~{per_step:.0f} s per step, 1 thread")
+    if wl.specs[0].dim == 2:
+        sample = (f"oracle L1 steps of the instance with half the modes per axis, ~{per_step:.0f} s per step, "
+                  f"scaled by the oracle's K^2 Q cost to the full size, 1 thread")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -221,7 +261,9 @@ def main():
     psl1.load()
     fp64_tf, fp32_tf = psl1.psl1_probe_peaks()
 
-    wl = workloads.cfg2(B=args.batch, seed=args.seed + dist.rank)
+    wl = make_workload(args, dist.rank)
+    if wl.specs[0].dim == 2:
+        args.coarse = "l1"          # the learned correction is defined for 1D instances
     u0 = wl.u0_concat()
     d_u0 = torch.from_numpy(u0).to("cuda")
     torch.cuda.synchronize()
@@ -358,13 +400,17 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"FP64 oracle fine propagator F_n at n = P/2 of the first {ninst} instances "
                          f"({dt:.1f} s, history from the GPU serial solve)"}
+        if wl.specs[0].dim == 2:
+            cpu["sample"] = (f"FP64 oracle: {ninst} L1 steps of the instance with half the modes per axis "
+                             f"({dt:.1f} s), scaled by the oracle's K^2 Q cost to the full size")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": wl.name, "batch": wl.B, "P": wl.P, "precision": args.precision,
-                       "l2": "flushed (256 MB write) before every timed step", "seed": args.seed},
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "seed": wl.meta.get("seed", args.seed)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "rel_err_vs_serial_fp64": err, "stop_tol": tol, "iterations": iters_all,
             "coarse_propagator": coarse, "coarse_candidates": cands, "learned_training": train_info,

@@ -99,6 +99,7 @@ __device__ __forceinline__ Carve carve(const PathArgs& a, char* base)
     c.ms.z = at<float>(base, L.z);
     c.ms.red = at<float>(base, L.red);
     c.ms.flag = c.s.bad;
+    c.ms.part = at<df>(base, L.mpart);
     c.cg.x = at<float>(base, L.cgx);
     c.cg.r = at<float>(base, L.cgr);
     c.cg.p = at<float>(base, L.cgp);
@@ -162,6 +163,7 @@ SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int 
     L.cggs = pcg ? take(4 * (size_t)(2 * Kmax + 8)) : -1;
     L.cggh = pcg ? take(4 * (size_t)(2 * Kmax + 8)) : -1;
     L.cgpart = pcg ? take(4 * (size_t)(4 * NT)) : -1;
+    L.mpart = f64 ? -1 : take(8 * 2 * (size_t)NT);
     L.mz = take(8 * (size_t)MLP_MAX_IN);
     L.mh0 = take(8 * (size_t)MLP_MAX_WIDTH);
     L.mh1 = take(8 * (size_t)MLP_MAX_WIDTH);
@@ -479,8 +481,9 @@ __global__ void __launch_bounds__(NT) k_coarse_dataset(PathArgs a, const double*
 }
 
 template <bool D2>
-__global__ void __launch_bounds__(NT) k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units,
-                                               int nunits, int* counter, const int* nfirst, const int* active)
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nunits, int* counter,
+         const int* nfirst, const int* active)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);
@@ -500,9 +503,9 @@ __global__ void __launch_bounds__(NT) k_fstage(PathArgs a, const double* Uold, d
 }
 
 template <bool D2>
-__global__ void __launch_bounds__(NT) k_coarse_sweep(PathArgs a, const double* u0, const double* Uold,
-                                                     double* Unew, const double* Fv, double* Gold, int init,
-                                                     const int* nfirst, const int* active, double* incr)
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_coarse_sweep(PathArgs a, const double* u0, const double* Uold, double* Unew, const double* Fv, double* Gold,
+               int init, const int* nfirst, const int* active, double* incr)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);
@@ -576,7 +579,8 @@ __global__ void __launch_bounds__(NT) k_coarse_sweep(PathArgs a, const double* u
 }
 
 template <bool D2>
-__global__ void __launch_bounds__(NT) k_serial_hyb(PathArgs a, const double* u0, double* Us)
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_serial_hyb(PathArgs a, const double* u0, double* Us)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);
@@ -621,8 +625,8 @@ __global__ void __launch_bounds__(NT) k_uni_hist(const InstDev* inst, const doub
 }
 
 template <bool D2>
-__global__ void __launch_bounds__(NT) k_uni_step(PathArgs a, double* Wcur, double* dW, double* Us, int j,
-                                                 const double* part, int chunk, int maxchunks)
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_uni_step(PathArgs a, double* Wcur, double* dW, double* Us, int j, const double* part, int chunk, int maxchunks)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);
@@ -651,8 +655,8 @@ __global__ void __launch_bounds__(NT) k_uni_step(PathArgs a, double* Wcur, doubl
 }
 
 template <bool D2>
-__global__ void __launch_bounds__(NT) k_one_step(PathArgs a, int ii, const double* c, const double* hist,
-                                                 double te, double mu, double* out)
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_one_step(PathArgs a, int ii, const double* c, const double* hist, double te, double mu, double* out)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);
@@ -669,7 +673,8 @@ __global__ void __launch_bounds__(NT) k_one_step(PathArgs a, int ii, const doubl
 }
 
 template <bool D2>
-__global__ void __launch_bounds__(NT) k_one_slice(PathArgs a, int ii, int n, const double* U, double* V)
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_one_slice(PathArgs a, int ii, int n, const double* U, double* V)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);
@@ -678,7 +683,8 @@ __global__ void __launch_bounds__(NT) k_one_slice(PathArgs a, int ii, int n, con
 }
 
 template <bool D2>
-__global__ void __launch_bounds__(NT) k_one_coarse(PathArgs a, int ii, int n, const double* U, double* out)
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_one_coarse(PathArgs a, int ii, int n, const double* U, double* out)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);
@@ -720,7 +726,8 @@ static cudaError_t launch_k(void (*k)(KA...), dim3 grid, size_t smem, cudaStream
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
 template <bool D2>
-__global__ void __launch_bounds__(NT) k_one_slice_noalloc(PathArgs a, int ii, int n, const double* U, double* V)
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_one_slice_noalloc(PathArgs a, int ii, int n, const double* U, double* V)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);

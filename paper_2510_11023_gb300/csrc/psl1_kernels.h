@@ -20,6 +20,7 @@ struct SmemLayout {
     int cur, hist, nxt, F, v, wp, wm, fp, fm, g, bad;     // FP64 path (+ common)
     int cdf, wpd, wmd, fpd, fmd, gdf, ydf, x, rhs, z, red, fac;   // FP32-pipe path
     int cgx, cgr, cgp, cgq, cgpl, cgdinv, cgred, cggs, cggh, cgpart;   // PCG inner solver
+    int mpart;                                                   // split-transform partial sums
     int mz, mh0, mh1;                                            // learned correction inference
     int total;
 };

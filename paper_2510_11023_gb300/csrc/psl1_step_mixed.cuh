@@ -38,6 +38,7 @@ struct MixSmem {
     float* z;     // Kp  FP32 correction
     float* red;   // NT/32 reduction scratch
     int* flag;    // [0] first bad pivot, [1] PCG iterations, [2] refinement residuals of the step
+    df* part;     // 2 NT: partial sums of the split transforms
 };
 
 __device__ __forceinline__ float block_max(float v, float* red)
@@ -52,6 +53,73 @@ __device__ __forceinline__ float block_max(float v, float* red)
     return m;
 }
 
+// acc += v (double-float), used to add split partial sums
+__device__ __forceinline__ void dfacc_add(dfacc& acc, df v)
+{
+    float s, e;
+    two_sum(acc.hi, v.hi, s, e);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, v.lo));
+}
+
+// Double-float transform of a table in global memory (L2-resident), one of
+//   TWO:  y0[o] = sum_{i even} A[i lda + o] x0[i],   y1[o] = sum_{i odd} A[i lda + o] x0[i]
+//   else: y0[o] = sum_i A[i lda + o] (o odd ? x1[i] : x0[i])
+// for o < nout, i < n; x in shared memory.  A thread owns an output column
+// (loads coalesced across the warp) and issues its table loads eight at a
+// time ahead of the multiply-adds, so eight L2 requests per thread are in
+// flight.  With fewer than NT/2 outputs the i range is split over several
+// threads (an even number of rows each) and the partial sums meet in `part`.
+template <bool TWO>
+__device__ void df_transform(const df* A, int lda, int n, int nout, const df* x0, const df* x1, df* y0, df* y1,
+                             df* part)
+{
+    const int t = threadIdx.x;
+    auto run = [&](int o, int i0, int i1, dfacc& a0, dfacc& a1) {
+        const df* xo = TWO ? x0 : ((o & 1) ? x1 : x0);
+        const df* col = A + o;
+        int i = i0;
+        for (; i + 8 <= i1; i += 8) {
+            df tv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) tv[j] = col[(size_t)(i + j) * lda];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) dfacc_fma((TWO && (j & 1)) ? a1 : a0, tv[j], xo[i + j]);
+        }
+        for (; i < i1; ++i) dfacc_fma((TWO && (i & 1)) ? a1 : a0, col[(size_t)i * lda], xo[i]);
+    };
+    if (2 * nout >= NT) {
+        for (int o = t; o < nout; o += NT) {
+            dfacc a0{0.f, 0.f}, a1{0.f, 0.f};
+            run(o, 0, n, a0, a1);
+            y0[o] = dfacc_result(a0);
+            if (TWO) y1[o] = dfacc_result(a1);
+        }
+        return;
+    }
+    const int S = NT / nout < 8 ? NT / nout : 8;
+    const int L = ((n + S - 1) / S + 1) & ~1;   // even, so that blocks of eight start on even i
+    const int o = t % nout, sp = t / nout;
+    if (sp < S) {
+        dfacc a0{0.f, 0.f}, a1{0.f, 0.f};
+        const int i0 = sp * L, i1 = i0 + L < n ? i0 + L : n;
+        if (i0 < i1) run(o, i0, i1, a0, a1);
+        part[2 * (sp * nout + o)] = dfacc_result(a0);
+        part[2 * (sp * nout + o) + 1] = dfacc_result(a1);
+    }
+    __syncthreads();
+    if (t < nout) {
+        dfacc a0{0.f, 0.f}, a1{0.f, 0.f};
+        for (int q = 0; q < S; ++q) {
+            dfacc_add(a0, part[2 * (q * nout + t)]);
+            dfacc_add(a1, part[2 * (q * nout + t) + 1]);
+        }
+        y0[t] = dfacc_result(a0);
+        if (TWO) y1[t] = dfacc_result(a1);
+    }
+    __syncthreads();
+}
+
 // nodes + moments + load.  fp32_only: D and f in FP32.
 __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const double* tp, const double* c,
                                     double te, MixSmem& ms, double* F, bool fp32_only)
@@ -64,20 +132,12 @@ __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const do
     const double mid2 = I.lo0 + I.hi0;
     for (int k = tid; k < K; k += NT) ms.cdf[k] = df_from_double(c[k]);
     __syncthreads();
+    // u at the node pairs: the odd-mode sum O (k even) into wpd, the even-mode sum E into wmd
+    df_transform<true>(Std, Qh, K, Qh, ms.cdf, nullptr, ms.wpd, ms.wmd, ms.part);
+    __syncthreads();
     for (int q = tid; q < Qh; q += NT) {
-        double ua, ub;
-        {
-            dfacc O{0.f, 0.f}, E{0.f, 0.f};
-            int k = 0;
-            for (; k + 1 < K; k += 2) {
-                dfacc_fma(O, Std[(size_t)k * Qh + q], ms.cdf[k]);
-                dfacc_fma(E, Std[(size_t)(k + 1) * Qh + q], ms.cdf[k + 1]);
-            }
-            if (k < K) dfacc_fma(O, Std[(size_t)k * Qh + q], ms.cdf[k]);
-            double o = df_to_double(dfacc_result(O)), e = df_to_double(dfacc_result(E));
-            ua = o + e;
-            ub = o - e;
-        }
+        const double o = df_to_double(ms.wpd[q]), e = df_to_double(ms.wmd[q]);
+        const double ua = o + e, ub = o - e;
         double xa = xh[q], xb = mid2 - xa, w = wh[q];
         double Da, Db, fa, fb;
         if (!fp32_only) {
@@ -101,21 +161,15 @@ __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const do
         ms.fmd[q] = df_from_double(w * (fa - fb));
     }
     __syncthreads();
-    const df* Cd = reinterpret_cast<const df*>(tp + Tb.oCd);
-    const df* Sd = reinterpret_cast<const df*>(tp + Tb.oSd);
+    // moments g_s (even s: w (D_q + D_q'), odd s: w (D_q - D_q')) and the load (even k: f_q + f_q')
     const int ns = 2 * K + 1;
-    for (int sI = tid; sI < ns; sI += NT) {
-        const df* wv = (sI & 1) ? ms.wmd : ms.wpd;
-        dfacc acc{0.f, 0.f};
-        for (int q = 0; q < Qh; ++q) dfacc_fma(acc, Cd[(size_t)q * ns + sI], wv[q]);
-        ms.gdf[sI] = dfacc_result(acc);
-    }
-    for (int k = tid; k < K; k += NT) {
-        const df* fv = (k & 1) ? ms.fmd : ms.fpd;
-        dfacc acc{0.f, 0.f};
-        for (int q = 0; q < Qh; ++q) dfacc_fma(acc, Sd[(size_t)q * K + k], fv[q]);
-        F[k] = df_to_double(dfacc_result(acc));
-    }
+    df_transform<false>(reinterpret_cast<const df*>(tp + Tb.oCd), ns, Qh, ns, ms.wpd, ms.wmd, ms.gdf, nullptr,
+                        ms.part);
+    __syncthreads();
+    df_transform<false>(reinterpret_cast<const df*>(tp + Tb.oSd), K, Qh, K, ms.fpd, ms.fmd, ms.ydf, nullptr,
+                        ms.part);
+    __syncthreads();
+    for (int k = tid; k < K; k += NT) F[k] = df_to_double(ms.ydf[k]);
     __syncthreads();
 }
 
