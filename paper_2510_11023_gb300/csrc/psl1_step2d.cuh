@@ -507,7 +507,7 @@ __device__ void pcg2d(const Dims2& g, const Tabs2<Nm>& tb, typename Nm::V mu, co
 }
 
 constexpr int PCG2_MAXIT32 = 60;
-constexpr float PCG2_RTOL32 = 1e-6f;
+constexpr float PCG2_RTOL32 = 1e-7f;
 constexpr int PCG2_MAXIT64 = 1000;
 constexpr double PCG2_RTOL64 = 1e-14;
 
@@ -618,6 +618,7 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
     }
     __syncthreads();
     pcg2d<NumF, 2, 4, 4>(g, tf, (float)mu, S.wd32, S.z, S, flag, PCG2_MAXIT32, PCG2_RTOL32);
+    float zprev = 0.f;
     for (int sweep = 0;; ++sweep) {
         float zmax = 0.f, xmax = 0.f;
         for (int k = tid; k < K; k += NT) {
@@ -628,7 +629,11 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
         }
         zmax = block_maxT(zmax, red);
         xmax = block_maxT(xmax, red);
-        if (fp32_only || zmax <= 1e-11f * xmax || sweep >= 6 || flag[0] >= 0) break;
+        // stop on a small correction, or when the observed contraction predicts one (as in 1D)
+        const bool small = zmax <= REFINE_TOL * xmax;
+        const bool predicted = sweep >= 1 && zmax < zprev && zmax * zmax <= REFINE_EST * xmax * zprev;
+        if (fp32_only || small || predicted || sweep >= 6 || flag[0] >= 0) break;
+        zprev = zmax;
         if (tid == 0) flag[2] += 1;
         // residual rhs - (I + mu A) x with A applied in double-float
         for (int k = tid; k < K; k += NT) S.cdf[k] = df_from_double(S.xr[k]);

@@ -6,13 +6,15 @@
 //     accumulated in double-float (unevaluated FP32 pairs, ~48-bit
 //     significand) from double-float tables;
 //   * D and f are evaluated in FP64 at the nodes (Q evaluations per step);
-//   * the SPD matrix I + mu cA k l (g_|k-l| + g_{k+l}) is factored in FP32
+//   * the inner solver works on the FP32 operator I + mu cA k l (g_|k-l| + g_{k+l}):
+//     Jacobi-preconditioned CG (default), or an FP32 Cholesky factor
 //     (block-packed lower storage in shared memory when it fits);
 //   * iterative refinement: r = rhs - M x with M applied in double-float
 //     through the Toeplitz+Hankel form, z = M32^{-1} r in FP32, x += z, until
-//     max|z| <= 1e-11 max|x| (at most 6 sweeps).  The FP32 factor is only a
-//     preconditioner; the fixed point is the solution of the FP64-accurate
-//     system.
+//     max|z| <= 1e-11 max|x|, or until the contraction of the last two
+//     corrections puts the next one below 1e-13 max|x| (at most 6 sweeps).
+//     The FP32 solver is only a preconditioner; the fixed point is the
+//     solution of the FP64-accurate system.
 // PSL1_PREC_FP32 runs the same kernel with D and f evaluated in FP32 and a
 // single FP32 solve (no refinement).  Its transforms stay double-float: a
 // plain FP32 moment loop was found to produce wrong moments under ptxas -O3
@@ -374,7 +376,12 @@ __device__ void chol32_solve_inv(BPack<float, MIX_LDB> A, int nb, float* v)
 // has condition number about D_+/D_-, so a few iterations reduce the residual
 // by FP32's resolution.  r: ms.z on entry; result in ms.z.
 constexpr int PCG_MAXIT = 40;
-constexpr float PCG_RTOL = 1e-6f;
+constexpr float PCG_RTOL = 1e-7f;
+// Refinement stops when the last correction is below REFINE_TOL of the
+// iterate, or when the contraction it shows (rho = |z_k| / |z_{k-1}|) puts the
+// next correction, rho |z_k|, below REFINE_EST of the iterate.
+constexpr float REFINE_TOL = 1e-11f;
+constexpr float REFINE_EST = 1e-13f;
 
 struct PcgSmem {
     float *x, *r, *p, *q, *pl, *dinv;   // Kp each
@@ -582,6 +589,7 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
     } else {
         pcg32(I, mu, ms, cg, PCG_MAXIT, PCG_RTOL);
     }
+    float zprev = 0.f;
     for (int sweep = 0;; ++sweep) {
         float zmax = 0.f, xmax = 0.f;
         for (int k = tid; k < I.K; k += NT) {
@@ -593,7 +601,10 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
         zmax = block_max(zmax, ms.red);
         __syncthreads();
         xmax = block_max(xmax, ms.red);
-        if (fp32_only || zmax <= 1e-11f * xmax || sweep >= 6 || *s.bad >= 0) break;
+        const bool small = zmax <= REFINE_TOL * xmax;
+        const bool predicted = sweep >= 1 && zmax < zprev && zmax * zmax <= REFINE_EST * xmax * zprev;
+        if (fp32_only || small || predicted || sweep >= 6 || *s.bad >= 0) break;
+        zprev = zmax;
         if (tid == 0) ms.flag[2] += 1;
         residual_df(I, mu, ms);
         if (inner == INNER_CHOL)
