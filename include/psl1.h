@@ -162,6 +162,19 @@ psl1_status psl1_get_errlog(psl1_h h, int b, double* out, int cap, int* len);
 psl1_status psl1_keep_iterates(psl1_h h, int on);
 psl1_status psl1_get_iterate(psl1_h h, int k, double* out);
 
+/* Graph mode of psl1_solve_parareal (on != 0; off by default): the whole
+ * iteration -- F stage, correction sweep, and a one-CTA update that logs e_k,
+ * retires converged instances and decides whether to continue -- runs as one
+ * CUDA graph whose while loop is driven from the device (a conditional graph
+ * node), so the host waits once per solve instead of once per iteration.
+ * Results, iteration counts and increment logs are the same as in the host
+ * loop (the kernels are the same and deterministic).  Per-kernel device times
+ * (psl1_stats.ms_fine / ms_coarse) are not measured in this mode (0).  The
+ * graph is built on the first graph-mode solve and rebuilt after
+ * psl1_set_coarse; with psl1_keep_iterates on, the host loop is used.
+ * No counterpart in the paper (its iteration is the same, Fig. parareal).     */
+psl1_status psl1_set_graph(psl1_h h, int on);
+
 /* Statistics of the last solve.                                             */
 psl1_status psl1_get_stats(psl1_h h, psl1_stats* st);
 

@@ -54,6 +54,12 @@ struct psl1_problem {
     // uniform solver pools (lazy)
     double *d_Wcur = nullptr, *d_dW = nullptr, *d_part = nullptr;
     int uni_chunk = 256, uni_maxchunks = 0;
+    cudaGraphExec_t uni_graph = nullptr;   // the uniform solver's N-step launch sequence
+    // graph-mode parareal (device-driven while loop)
+    bool graph_mode = false;
+    cudaGraphExec_t par_graph = nullptr;
+    int *d_iters = nullptr, *d_kstate = nullptr;
+    double *d_errlog = nullptr, *d_tol = nullptr;
     PathArgs pa{};
     // state
     bool u0_set = false, par_done = false, ser_done = false;
@@ -158,6 +164,8 @@ void psl1_destroy(psl1_h h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->uni_graph) cudaGraphExecDestroy(h->uni_graph);
+    if (h->par_graph) cudaGraphExecDestroy(h->par_graph);
     for (void* p : h->allocs) cudaFree(p);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
@@ -542,6 +550,20 @@ static void count_work(psl1_problem* h, const std::vector<int>& nfirst, const st
     }
 }
 
+// The uniform solver's launches: initial state, then per fine step j the
+// history partial sums and the step (j = 0 has no history).
+static cudaError_t enqueue_uniform(psl1_problem* h)
+{
+    cudaError_t e = launch_uni_init(h->pa, h->B, h->d_u0, h->d_Wcur, h->d_Us, h->stream);
+    for (int j = 0; j < h->Nmax && e == cudaSuccess; ++j) {
+        e = launch_uni_hist(h->pa, h->B, h->d_dW, j, h->d_part, h->uni_chunk, h->uni_maxchunks, h->stream);
+        if (e == cudaSuccess)
+            e = launch_uni_step(h->pa, h->B, h->d_Wcur, h->d_dW, h->d_Us, j, h->d_part, h->uni_chunk,
+                                h->uni_maxchunks, h->stream);
+    }
+    return e;
+}
+
 psl1_status psl1_solve_serial(psl1_h h, int kind)
 {
     if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
@@ -564,15 +586,25 @@ psl1_status psl1_solve_serial(psl1_h h, int kind)
         h->stats.kernel_launches = 1;
     } else if (kind == PSL1_SERIAL_UNIFORM) {
         TRY(ensure_uniform_pools(h));
-        CU(h, launch_uni_init(h->pa, h->B, h->d_u0, h->d_Wcur, h->d_Us, h->stream));
-        int launches = 1;
-        for (int j = 0; j < h->Nmax; ++j) {
-            CU(h, launch_uni_hist(h->pa, h->B, h->d_dW, j, h->d_part, h->uni_chunk, h->uni_maxchunks, h->stream));
-            CU(h, launch_uni_step(h->pa, h->B, h->d_Wcur, h->d_dW, h->d_Us, j, h->d_part, h->uni_chunk,
-                                  h->uni_maxchunks, h->stream));
-            launches += (j > 0) ? 2 : 1;
+        // The N-step sequence (a history launch and a step launch per fine step) is
+        // captured into a CUDA graph on the first uniform solve of the handle and
+        // replayed afterwards: every argument is a fixed pool or a step index, and
+        // u0, D and f are read from device memory when the graph runs.
+        if (!h->uni_graph) {
+            cudaGraph_t g = nullptr;
+            CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_uniform(h);
+            cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
+            if (e == cudaSuccess) e = ee;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->uni_graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                h->uni_graph = nullptr;
+                return fail(h, PSL1_ERR_CUDA, "uniform solver graph: %s", cudaGetErrorString(e));
+            }
         }
-        h->stats.kernel_launches = launches;
+        CU(h, cudaGraphLaunch(h->uni_graph, h->stream));
+        h->stats.kernel_launches = 2 * h->Nmax;   // init + (N - 1) history + N step kernels
         for (int b = 0; b < h->B; ++b) {
             h->stats.fine_steps += h->inst[b].N;
             h->stats.fine_step_modes += (double)h->inst[b].N * h->inst[b].K;
@@ -605,6 +637,128 @@ static psl1_status snapshot(psl1_problem* h, const double* d)
     return PSL1_OK;
 }
 
+// Convergence verdict and statistics shared by the host-loop and graph modes.
+static psl1_status finish_parareal(psl1_problem* h, double tol, int maxit, int* iters_out,
+                                   std::chrono::steady_clock::time_point t0)
+{
+    h->par_done = true;
+    int itmax = 0;
+    bool all_conv = true;
+    for (int b = 0; b < h->B; ++b) {
+        itmax = std::max(itmax, h->iters[b]);
+        bool conv = (!h->errlog[b].empty() && h->errlog[b].back() <= tol) || h->iters[b] >= h->P;
+        if (!conv) all_conv = false;
+    }
+    TRY(read_flops(h));
+    h->stats.iterations_max = itmax;
+    if (iters_out) *iters_out = itmax;
+    h->stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (!all_conv) return fail(h, PSL1_ERR_NOT_CONVERGED, "parareal stopped at max_iter=%d above tol", maxit);
+    return PSL1_OK;
+}
+
+psl1_status psl1_set_graph(psl1_h h, int on)
+{
+    if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
+    h->graph_mode = on != 0;
+    return PSL1_OK;
+}
+
+// The graph-mode iteration: a while node whose body is
+//   F stage (U^k -> F_old), correction sweep (U^k -> U^{k+1}, e_k), U^k <- U^{k+1},
+//   update (log e_k, retire converged instances, k += 1, loop condition).
+static psl1_status build_parareal_graph(psl1_problem* h)
+{
+    if (!h->d_iters) {
+        TRY(dalloc(h, &h->d_iters, h->B));
+        TRY(dalloc(h, &h->d_kstate, 2));
+        TRY(dalloc(h, &h->d_errlog, (size_t)h->B * h->P));
+        TRY(dalloc(h, &h->d_tol, 1));
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle cond;
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t wnode;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const int grid = std::min(h->nunits, h->pa.nslots);
+            cudaError_t q = launch_fstage(h->pa, h->d_Ua, h->d_Fv, h->d_units, h->nunits, h->d_counter, h->d_nfirst,
+                                          h->d_active, grid, h->stream);
+            if (q == cudaSuccess)
+                q = launch_coarse_sweep(h->pa, h->B, h->d_u0, h->d_Ua, h->d_Ub, h->d_Fv, h->d_Gold, 0, h->d_nfirst,
+                                        h->d_active, h->d_incr, h->stream);
+            if (q == cudaSuccess)
+                q = cudaMemcpyAsync(h->d_Ua, h->d_Ub, sizeof(double) * h->sumU, cudaMemcpyDeviceToDevice, h->stream);
+            if (q == cudaSuccess)
+                q = launch_pr_update(h->d_incr, h->d_active, h->d_nfirst, h->d_iters, h->d_errlog, h->d_counter,
+                                     h->d_kstate, h->d_tol, cond, h->B, h->P, h->stream);
+            cudaGraph_t out = nullptr;
+            e = cudaStreamEndCapture(h->stream, &out);
+            if (e == cudaSuccess) e = q;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->par_graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->par_graph = nullptr;
+        return fail(h, PSL1_ERR_CUDA, "parareal graph: %s", cudaGetErrorString(e));
+    }
+    return PSL1_OK;
+}
+
+static psl1_status solve_parareal_graph(psl1_problem* h, double tol, int maxit)
+{
+    const int B = h->B, P = h->P;
+    if (!h->par_graph) TRY(build_parareal_graph(h));
+    std::vector<int> zeros(B, 0), ones(B, 1);
+    const int kst[2] = {0, maxit};
+    CU(h, cudaMemcpyAsync(h->d_active, ones.data(), sizeof(int) * B, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaEventRecord(h->ev[0], h->stream));
+    CU(h, launch_coarse_sweep(h->pa, B, h->d_u0, nullptr, h->d_Ua, nullptr, h->d_Gold, 1, h->d_nfirst, h->d_active,
+                              h->d_incr, h->stream));
+    CU(h, cudaMemcpyAsync(h->d_nfirst, zeros.data(), sizeof(int) * B, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->d_iters, zeros.data(), sizeof(int) * B, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->d_kstate, kst, sizeof kst, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->d_tol, &tol, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
+    CU(h, cudaGraphLaunch(h->par_graph, h->stream));
+    CU(h, cudaEventRecord(h->ev[1], h->stream));
+    std::vector<int> iters(B);
+    std::vector<double> elog((size_t)B * P);
+    CU(h, cudaMemcpyAsync(iters.data(), h->d_iters, sizeof(int) * B, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaMemcpyAsync(elog.data(), h->d_errlog, sizeof(double) * elog.size(), cudaMemcpyDeviceToHost,
+                          h->stream));
+    TRY(check_device_status(h));
+    int itmax = 0;
+    for (int b = 0; b < B; ++b) {
+        h->iters[b] = iters[b];
+        h->errlog[b].assign(elog.begin() + (size_t)b * P, elog.begin() + (size_t)b * P + iters[b]);
+        itmax = std::max(itmax, iters[b]);
+    }
+    std::vector<int> nfirst(B), active(B);
+    for (int k = 0; k < itmax; ++k) {
+        for (int b = 0; b < B; ++b) {
+            nfirst[b] = k;
+            active[b] = iters[b] > k;
+        }
+        count_work(h, nfirst, active);
+    }
+    h->stats.kernel_launches = 1 + 3 * itmax;
+    h->d_Ucur = h->d_Ua;
+    return PSL1_OK;
+}
+
 psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_out)
 {
     if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
@@ -618,6 +772,10 @@ psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_o
     h->iters.assign(B, 0);
     h->errlog.assign(B, {});
     TRY(reset_status(h));
+    if (h->graph_mode && !h->keep_iterates) {
+        TRY(solve_parareal_graph(h, tol, maxit));
+        return finish_parareal(h, tol, maxit, iters_out, t0);
+    }
     std::vector<int> nfirst(B, 0), active(B, 1);
     std::vector<double> incr(B, 0.0);
     double* Uk = h->d_Ua;
@@ -670,20 +828,7 @@ psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_o
         }
     }
     h->d_Ucur = Uk;
-    h->par_done = true;
-    int itmax = 0;
-    bool all_conv = true;
-    for (int b = 0; b < B; ++b) {
-        itmax = std::max(itmax, h->iters[b]);
-        bool conv = (!h->errlog[b].empty() && h->errlog[b].back() <= tol) || h->iters[b] >= P;
-        if (!conv) all_conv = false;
-    }
-    TRY(read_flops(h));
-    h->stats.iterations_max = itmax;
-    if (iters_out) *iters_out = itmax;
-    h->stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (!all_conv) return fail(h, PSL1_ERR_NOT_CONVERGED, "parareal stopped at max_iter=%d above tol", maxit);
-    return PSL1_OK;
+    return finish_parareal(h, tol, maxit, iters_out, t0);
 }
 
 psl1_status psl1_get_coeffs(psl1_h h, int which, double* out)
@@ -1171,11 +1316,19 @@ psl1_status psl1_set_coarse(psl1_h h, psl1_mlp_h mh)
     if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
     if (!mh) {
         h->pa.mlp = MlpDev{};
+        if (h->par_graph) {
+            cudaGraphExecDestroy(h->par_graph);
+            h->par_graph = nullptr;
+        }
         return PSL1_OK;
     }
     if (h->pa.dim2) return fail(h, PSL1_ERR_ARG, "the learned coarse correction is defined for 1D instances");
     if (mh->stream != h->stream) CU(h, cudaStreamSynchronize(mh->stream));
     h->pa.mlp = mh->dev();
+    if (h->par_graph) {   // the graph holds the kernels' arguments
+        cudaGraphExecDestroy(h->par_graph);
+        h->par_graph = nullptr;
+    }
     return PSL1_OK;
 }
 

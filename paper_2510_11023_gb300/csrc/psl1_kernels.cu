@@ -693,6 +693,40 @@ k_one_coarse(PathArgs a, int ii, int n, const double* U, double* out)
     for (int k = threadIdx.x; k < I.K; k += NT) out[k] = cv.nxt[k];
 }
 
+__global__ void k_pr_update(const double* incr, int* active, int* nfirst, int* iters, double* errlog, int* counter,
+                            int* kstate, const double* tol, cudaGraphConditionalHandle cond, int B, int P)
+{
+    __shared__ int s_act;
+    if (threadIdx.x == 0) s_act = 0;
+    __syncthreads();
+    const int k = kstate[0];
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        if (active[b]) {
+            errlog[(size_t)b * P + k] = incr[b];
+            iters[b] = k + 1;
+            if (incr[b] <= *tol)
+                active[b] = 0;
+            else
+                atomicAdd(&s_act, 1);
+        }
+        nfirst[b] = k + 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        kstate[0] = k + 1;
+        *counter = 0;
+        cudaGraphSetConditional(cond, (s_act > 0 && k + 1 < kstate[1]) ? 1u : 0u);
+    }
+}
+
+cudaError_t launch_pr_update(const double* incr, int* active, int* nfirst, int* iters, double* errlog, int* counter,
+                             int* kstate, const double* tol, cudaGraphConditionalHandle cond, int B, int P,
+                             cudaStream_t s)
+{
+    k_pr_update<<<1, 256, 0, s>>>(incr, active, nfirst, iters, errlog, counter, kstate, tol, cond, B, P);
+    return cudaGetLastError();
+}
+
 static PathArgs slot(const PathArgs& a, int s)
 {
     PathArgs b = a;

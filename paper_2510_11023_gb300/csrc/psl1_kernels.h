@@ -102,6 +102,14 @@ cudaError_t launch_iterate_dataset(const PathArgs& a, int B, int P, const double
                                    const double* Gold, const int* nfirst, float* Z, float* R, long long base,
                                    cudaStream_t s);
 
+// Device-side bookkeeping of one parareal iteration inside the graph-mode loop:
+// log the increments, retire converged instances, advance k and nfirst, reset the
+// unit counter, and set the while-loop condition (any instance active and k < maxit).
+// kstate = {k, maxit}.
+cudaError_t launch_pr_update(const double* incr, int* active, int* nfirst, int* iters, double* errlog, int* counter,
+                             int* kstate, const double* tol, cudaGraphConditionalHandle cond, int B, int P,
+                             cudaStream_t s);
+
 // Single slice with scratch from a fixed device array (no allocation).
 constexpr long long NOALLOC_SCRATCH_DOUBLES = 512 * 1024;   // 4 MiB
 cudaError_t launch_one_slice_noalloc(const PathArgs& a, int b, int n, const double* U, double* V,
