@@ -173,6 +173,22 @@ void psl1_destroy(psl1_h h)
     delete h;
 }
 
+// dpar / fpar as (hi, lo) float pairs for the double-float evaluation, and
+// whether f reduces to its polynomial term
+static void family_copies(InstDev& I)
+{
+    for (int i = 0; i < 8; ++i) {
+        float h = (float)I.dpar[i];
+        I.dpf[2 * i] = h;
+        I.dpf[2 * i + 1] = (float)(I.dpar[i] - (double)h);
+        h = (float)I.fpar[i];
+        I.fpf[2 * i] = h;
+        I.fpf[2 * i + 1] = (float)(I.fpar[i] - (double)h);
+    }
+    const double* c = I.fpar;
+    I.f_poly = (c[0] == 0.0 && c[1] == 0.0 && c[3] == 0.0 && c[4] == 0.0 && c[5] == 0.0) ? 1 : 0;
+}
+
 static psl1_status validate(const psl1_instance& d, int P, int b)
 {
     if (d.dim != 1 && d.dim != 2) return fail(nullptr, PSL1_ERR_ARG, "instance %d: dim must be 1 or 2", b);
@@ -285,6 +301,12 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         o += (mq + 1) / 2;
         t.oAux2 = o;
         o += 2LL * t.Qh;
+        t.oWd = o;
+        o += t.Qh;
+        t.oAuxd = o;
+        o += 4LL * t.Qh;
+        t.oAux2d = o;
+        o += 2LL * t.Qh;
         h->tabElems = o;
         int id = (int)h->tabs.size();
         h->tabs.push_back(t);
@@ -328,6 +350,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
             I.dpar[i] = d.dpar[i];
             I.fpar[i] = d.fpar[i];
         }
+        family_copies(I);
         I.tab = table_for(I.Mx, I.Q, I.lo0, I.hi0);
         if (I.dim == 2) {
             I.lo1 = d.lo[1];
@@ -431,6 +454,9 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         jobs[t].St32 = h->d_tp + T.oSt32;
         jobs[t].Dt32 = h->d_tp + T.oDt32;
         jobs[t].aux2 = h->d_tp + T.oAux2;
+        jobs[t].Wd = h->d_tp + T.oWd;
+        jobs[t].auxd = h->d_tp + T.oAuxd;
+        jobs[t].aux2d = h->d_tp + T.oAux2d;
     }
     auto cu = [&](cudaError_t e2, const char* what) -> psl1_status {
         if (e2 != cudaSuccess) return fail(h, PSL1_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e2));
@@ -486,8 +512,10 @@ psl1_status psl1_set_D(psl1_h h, const double* dpar)
 {
     if (!h || !dpar) return fail(h, PSL1_ERR_ARG, "NULL argument");
     if (!finite_all(dpar, 8 * h->B)) return fail(h, PSL1_ERR_ARG, "non-finite D parameters");
-    for (int b = 0; b < h->B; ++b)
+    for (int b = 0; b < h->B; ++b) {
         for (int i = 0; i < 8; ++i) h->inst[b].dpar[i] = h->desc[b].dpar[i] = dpar[8 * b + i];
+        family_copies(h->inst[b]);
+    }
     CU(h, cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(InstDev) * h->B, cudaMemcpyHostToDevice, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
     return PSL1_OK;
@@ -497,8 +525,10 @@ psl1_status psl1_set_f(psl1_h h, const double* fpar)
 {
     if (!h || !fpar) return fail(h, PSL1_ERR_ARG, "NULL argument");
     if (!finite_all(fpar, 8 * h->B)) return fail(h, PSL1_ERR_ARG, "non-finite f parameters");
-    for (int b = 0; b < h->B; ++b)
+    for (int b = 0; b < h->B; ++b) {
         for (int i = 0; i < 8; ++i) h->inst[b].fpar[i] = h->desc[b].fpar[i] = fpar[8 * b + i];
+        family_copies(h->inst[b]);
+    }
     CU(h, cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(InstDev) * h->B, cudaMemcpyHostToDevice, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
     return PSL1_OK;

@@ -41,7 +41,8 @@ struct InstDev {
     long long oW;                // offset in N*K fine-history pools (uniform solver)
     int Nb;                      // b(j) table length - 1 (max of N, P, m)
     int Qy, Qhy, tabY;           // y axis (2D): nodes, mirror pairs, table set
-    int pad_;
+    int f_poly;                  // f has only its polynomial term c2 u (1-u)
+    float dpf[16], fpf[16];      // dpar, fpar as double-float pairs (hi, lo)
 };
 
 struct TabDev {
@@ -57,6 +58,7 @@ struct TabDev {
     long long oDtd;  // the same as double-float pairs
     long long oSt32, oDt32;   // Mx x Qh FP32 copies of St and Dt (two floats per slot)
     long long oAux2; // 2*Qh: cos(2 pi x) at x_q and at the mirror node
+    long long oWd, oAuxd, oAux2d;   // Qh weights, 4*Qh aux, 2*Qh aux2 as double-float pairs
 };
 
 // Device error word: the first failure wins.  code < 0 is a psl1_status.

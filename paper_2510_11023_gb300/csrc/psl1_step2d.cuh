@@ -24,29 +24,9 @@
 #pragma once
 #include "psl1_step.cuh"
 #include "psl1_step_mixed.cuh"
+#include "psl1_dfmath.cuh"
 
 namespace psl1 {
-
-// ------------------------------------------------------------------ double-float helpers
-__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
-
-// a + b; the low part is left unnormalised (it only feeds further double-float
-// operations, which take the hi part exactly and the lo part as a correction)
-__device__ __forceinline__ df df_add(df a, df b)
-{
-    float s, e;
-    two_sum(a.hi, b.hi, s, e);
-    return {s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
-}
-
-__device__ __forceinline__ df df_mul(df a, df b)
-{
-    float p = __fmul_rn(a.hi, b.hi);
-    float pe = __fmaf_rn(a.hi, b.hi, -p);
-    pe = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, pe));
-    float h = __fadd_rn(p, pe);
-    return {h, __fsub_rn(pe, __fsub_rn(h, p))};
-}
 
 // ------------------------------------------------------------------ number policies
 struct NumF {
@@ -390,6 +370,28 @@ __device__ __forceinline__ Node2 node2(const InstDev& I, const TabDev& TX, const
     return n;
 }
 
+// The same node data as double-float, from the double-float tables
+struct Node2df {
+    df w, sx1, sx2, cy2;
+};
+
+__device__ __forceinline__ Node2df node2_df(const InstDev& I, const TabDev& TX, const TabDev& TY, const double* tp,
+                                            int i, int j)
+{
+    Node2df n;
+    const bool mx = i >= I.Qh, my = j >= I.Qhy;
+    const int qi = mx ? I.Q - 1 - i : i, qj = my ? I.Qy - 1 - j : j;
+    const df* wx = reinterpret_cast<const df*>(tp + TX.oWd);
+    const df* wy = reinterpret_cast<const df*>(tp + TY.oWd);
+    const df* ax = reinterpret_cast<const df*>(tp + TX.oAuxd);
+    const df* ay = reinterpret_cast<const df*>(tp + TY.oAux2d);
+    n.w = df_mul(wx[qi], wy[qj]);
+    n.sx1 = ax[4 * qi + (mx ? 2 : 0)];
+    n.sx2 = ax[4 * qi + (mx ? 3 : 1)];
+    n.cy2 = ay[2 * qj + (my ? 1 : 0)];
+    return n;
+}
+
 // ------------------------------------------------------------------ block reductions
 template <typename T>
 __device__ __forceinline__ void block_sum2T(T& a, T& b, T* red)
@@ -589,19 +591,30 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
     to_nodes<NumDF, 2, 2>(g, td, S.cdf, T1, N1);
     for (int e = tid; e < QQ; e += NT) {
         const int i = e / g.Qy, j = e - i * g.Qy;
-        const Node2 nd = node2(I, TX, TY, tp, i, j);
-        const double u = df_to_double(N1[e]);
-        double wD, wf;
         if (fp32_only) {
-            wD = nd.w * (double)D_eval2_32(I, (float)nd.sx1, (float)nd.sx2, (float)nd.cy2, (float)u);
-            wf = nd.w * (double)f_eval32(I, (float)nd.sx1, (float)te, (float)u);
-        } else {
-            wD = nd.w * D_eval2(I, nd.sx1, nd.sx2, nd.cy2, u);
-            wf = nd.w * f_eval(I, nd.x, nd.sx1, te, u);
+            const Node2 nd = node2(I, TX, TY, tp, i, j);
+            const double u = df_to_double(N1[e]);
+            const double wD = nd.w * (double)D_eval2_32(I, (float)nd.sx1, (float)nd.sx2, (float)nd.cy2, (float)u);
+            const double wf = nd.w * (double)f_eval32(I, (float)nd.sx1, (float)te, (float)u);
+            W[e] = df_from_double(wD);
+            S.wd32[e] = (float)wD;
+            N2[e] = df_from_double(wf);
+            continue;
         }
-        W[e] = df_from_double(wD);
-        S.wd32[e] = (float)wD;
-        N2[e] = df_from_double(wf);
+        // D (and a polynomial f) in double-float on the FP32 pipes; transcendental f in FP64
+        const Node2df nd = node2_df(I, TX, TY, tp, i, j);
+        const df u = N1[e];
+        const df wD = df_mul(nd.w, D_eval_df(I, nd.sx1, nd.sx2, nd.cy2, u));
+        df wf;
+        if (I.f_poly) {
+            wf = df_mul(nd.w, f_poly_df(I, u));
+        } else {
+            const Node2 n64 = node2(I, TX, TY, tp, i, j);
+            wf = df_from_double(n64.w * f_eval(I, n64.x, n64.sx1, te, df_to_double(u)));
+        }
+        W[e] = wD;
+        S.wd32[e] = wD.hi;
+        N2[e] = wf;
     }
     __syncthreads();
     from_nodes<NumDF, 2, 2>(g, td, N2, T2, S.cdf);

@@ -22,6 +22,7 @@
 // in double-float), so that loop form is not used.
 #pragma once
 #include "psl1_step.cuh"
+#include "psl1_dfmath.cuh"
 
 namespace psl1 {
 
@@ -67,57 +68,100 @@ __device__ __forceinline__ void dfacc_add(dfacc& acc, df v)
 // Double-float transform of a table in global memory (L2-resident), one of
 //   TWO:  y0[o] = sum_{i even} A[i lda + o] x0[i],   y1[o] = sum_{i odd} A[i lda + o] x0[i]
 //   else: y0[o] = sum_i A[i lda + o] (o odd ? x1[i] : x0[i])
-// for o < nout, i < n; x in shared memory.  A thread owns an output column
-// (loads coalesced across the warp) and issues its table loads eight at a
-// time ahead of the multiply-adds, so eight L2 requests per thread are in
-// flight.  With fewer than NT/2 outputs the i range is split over several
-// threads (an even number of rows each) and the partial sums meet in `part`.
+// for o < nout, i < n; x in shared memory.  A thread owns output columns
+// (loads coalesced across the warp) and issues its table loads D rows at a
+// time ahead of the multiply-adds; R columns are walked together so that R D
+// L2 requests per thread are in flight.  Outputs are dealt out in full rounds
+// of NT (two columns per thread per pass); the columns of a last, partial
+// round split their rows over several threads, whose partial sums meet in
+// `part` (2 NT double-float entries).
+template <bool TWO, int R, int D>
+__device__ __forceinline__ void df_columns(const df* A, int lda, int i0, int i1, const int (&o)[R], int nout,
+                                           const df* x0, const df* x1, dfacc (&a0)[R], dfacc (&a1)[R])
+{
+    const df* col[R];
+    const df* xo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        col[r] = A + (o[r] < nout ? o[r] : 0);
+        xo[r] = TWO ? x0 : ((o[r] & 1) ? x1 : x0);
+    }
+    int i = i0;
+    for (; i + D <= i1; i += D) {
+        df tv[R][D];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < D; ++j) tv[r][j] = col[r][(size_t)(i + j) * lda];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < D; ++j) dfacc_fma((TWO && (j & 1)) ? a1[r] : a0[r], tv[r][j], xo[r][i + j]);
+    }
+    for (; i < i1; ++i)
+#pragma unroll
+        for (int r = 0; r < R; ++r) dfacc_fma((TWO && (i & 1)) ? a1[r] : a0[r], col[r][(size_t)i * lda], xo[r][i]);
+}
+
 template <bool TWO>
 __device__ void df_transform(const df* A, int lda, int n, int nout, const df* x0, const df* x1, df* y0, df* y1,
                              df* part)
 {
     const int t = threadIdx.x;
-    auto run = [&](int o, int i0, int i1, dfacc& a0, dfacc& a1) {
-        const df* xo = TWO ? x0 : ((o & 1) ? x1 : x0);
-        const df* col = A + o;
-        int i = i0;
-        for (; i + 8 <= i1; i += 8) {
-            df tv[8];
+    const int full = nout / NT, rem = nout - full * NT;
+    for (int g = 0; g < full;) {
+        if (full - g >= 2) {
+            const int o[2] = {t + g * NT, t + (g + 1) * NT};
+            dfacc a0[2] = {{0.f, 0.f}, {0.f, 0.f}}, a1[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            df_columns<TWO, 2, 8>(A, lda, 0, n, o, nout, x0, x1, a0, a1);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) tv[j] = col[(size_t)(i + j) * lda];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) dfacc_fma((TWO && (j & 1)) ? a1 : a0, tv[j], xo[i + j]);
+            for (int r = 0; r < 2; ++r) {
+                y0[o[r]] = dfacc_result(a0[r]);
+                if (TWO) y1[o[r]] = dfacc_result(a1[r]);
+            }
+            g += 2;
+        } else {
+            const int o[1] = {t + g * NT};
+            dfacc a0[1] = {{0.f, 0.f}}, a1[1] = {{0.f, 0.f}};
+            df_columns<TWO, 1, 16>(A, lda, 0, n, o, nout, x0, x1, a0, a1);
+            y0[o[0]] = dfacc_result(a0[0]);
+            if (TWO) y1[o[0]] = dfacc_result(a1[0]);
+            g += 1;
         }
-        for (; i < i1; ++i) dfacc_fma((TWO && (i & 1)) ? a1 : a0, col[(size_t)i * lda], xo[i]);
-    };
-    if (2 * nout >= NT) {
-        for (int o = t; o < nout; o += NT) {
-            dfacc a0{0.f, 0.f}, a1{0.f, 0.f};
-            run(o, 0, n, a0, a1);
-            y0[o] = dfacc_result(a0);
-            if (TWO) y1[o] = dfacc_result(a1);
+    }
+    if (rem == 0) return;
+    // last round: rem columns starting at base, rows split S ways
+    const int base = full * NT;
+    const int S = NT / rem < 8 ? NT / rem : 8;
+    if (S == 1) {   // rem >= NT/2: one thread per column
+        if (t < rem) {
+            const int o[1] = {base + t};
+            dfacc a0[1] = {{0.f, 0.f}}, a1[1] = {{0.f, 0.f}};
+            df_columns<TWO, 1, 16>(A, lda, 0, n, o, nout, x0, x1, a0, a1);
+            y0[o[0]] = dfacc_result(a0[0]);
+            if (TWO) y1[o[0]] = dfacc_result(a1[0]);
         }
         return;
     }
-    const int S = NT / nout < 8 ? NT / nout : 8;
-    const int L = ((n + S - 1) / S + 1) & ~1;   // even, so that blocks of eight start on even i
-    const int o = t % nout, sp = t / nout;
+    const int L = ((n + S - 1) / S + 1) & ~1;   // even, so that row blocks start on even i
+    const int c = t % rem, sp = t / rem;
     if (sp < S) {
-        dfacc a0{0.f, 0.f}, a1{0.f, 0.f};
+        const int o[1] = {base + c};
+        dfacc a0[1] = {{0.f, 0.f}}, a1[1] = {{0.f, 0.f}};
         const int i0 = sp * L, i1 = i0 + L < n ? i0 + L : n;
-        if (i0 < i1) run(o, i0, i1, a0, a1);
-        part[2 * (sp * nout + o)] = dfacc_result(a0);
-        part[2 * (sp * nout + o) + 1] = dfacc_result(a1);
+        if (i0 < i1) df_columns<TWO, 1, 8>(A, lda, i0, i1, o, nout, x0, x1, a0, a1);
+        part[2 * (sp * rem + c)] = dfacc_result(a0[0]);
+        part[2 * (sp * rem + c) + 1] = dfacc_result(a1[0]);
     }
     __syncthreads();
-    if (t < nout) {
+    if (t < rem) {
         dfacc a0{0.f, 0.f}, a1{0.f, 0.f};
         for (int q = 0; q < S; ++q) {
-            dfacc_add(a0, part[2 * (q * nout + t)]);
-            dfacc_add(a1, part[2 * (q * nout + t) + 1]);
+            dfacc_add(a0, part[2 * (q * rem + t)]);
+            dfacc_add(a1, part[2 * (q * rem + t) + 1]);
         }
-        y0[t] = dfacc_result(a0);
-        if (TWO) y1[t] = dfacc_result(a1);
+        y0[base + t] = dfacc_result(a0);
+        if (TWO) y1[base + t] = dfacc_result(a1);
     }
     __syncthreads();
 }
@@ -137,25 +181,44 @@ __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const do
     // u at the node pairs: the odd-mode sum O (k even) into wpd, the even-mode sum E into wmd
     df_transform<true>(Std, Qh, K, Qh, ms.cdf, nullptr, ms.wpd, ms.wmd, ms.part);
     __syncthreads();
-    for (int q = tid; q < Qh; q += NT) {
+    const df* wd = reinterpret_cast<const df*>(tp + Tb.oWd);
+    const df* auxd = reinterpret_cast<const df*>(tp + Tb.oAuxd);
+    for (int q = tid; q < Qh && !fp32_only; q += NT) {
+        // D (and a polynomial f) in double-float on the FP32 pipes; transcendental f in FP64
+        const df o = ms.wpd[q], e = ms.wmd[q];
+        const df ua = df_addn(o, e), ub = df_addn(o, df_neg(e));
+        const df zero{0.f, 0.f};
+        const df Da = D_eval_df(I, auxd[4 * q], auxd[4 * q + 1], zero, ua);
+        const df Db = D_eval_df(I, auxd[4 * q + 2], auxd[4 * q + 3], zero, ub);
+        df fs, fd;
+        if (I.f_poly) {
+            const df fa = f_poly_df(I, ua), fb = f_poly_df(I, ub);
+            fs = df_addn(fa, fb);
+            fd = df_addn(fa, df_neg(fb));
+        } else {
+            const double xa = xh[q], xb = mid2 - xa;
+            const double fa = f_eval(I, xa, aux[4 * q], te, df_to_double(ua));
+            const double fb = f_eval(I, xb, aux[4 * q + 2], te, df_to_double(ub));
+            fs = df_from_double(fa + fb);
+            fd = df_from_double(fa - fb);
+        }
+        const df w = wd[q];
+        ms.wpd[q] = df_mul(w, df_addn(Da, Db));
+        ms.wmd[q] = df_mul(w, df_addn(Da, df_neg(Db)));
+        ms.fpd[q] = df_mul(w, fs);
+        ms.fmd[q] = df_mul(w, fd);
+    }
+    for (int q = tid; q < Qh && fp32_only; q += NT) {
         const double o = df_to_double(ms.wpd[q]), e = df_to_double(ms.wmd[q]);
         const double ua = o + e, ub = o - e;
         double xa = xh[q], xb = mid2 - xa, w = wh[q];
-        double Da, Db, fa, fb;
-        if (!fp32_only) {
-            Da = D_eval(I, aux[4 * q], aux[4 * q + 1], ua);
-            Db = D_eval(I, aux[4 * q + 2], aux[4 * q + 3], ub);
-            fa = f_eval(I, xa, aux[4 * q], te, ua);
-            fb = f_eval(I, xb, aux[4 * q + 2], te, ub);
-        } else {
-            Da = D_eval32(I, (float)aux[4 * q], (float)aux[4 * q + 1], (float)ua);
-            Db = D_eval32(I, (float)aux[4 * q + 2], (float)aux[4 * q + 3], (float)ub);
-            fa = f_eval(I, xa, aux[4 * q], te, ua);   // sources keep FP64 (rarely used)
-            fb = f_eval(I, xb, aux[4 * q + 2], te, ub);
-            if (I.fpar[4] == 0.0 && I.fpar[5] == 0.0) {
-                fa = f_eval32(I, (float)aux[4 * q], (float)te, (float)ua);
-                fb = f_eval32(I, (float)aux[4 * q + 2], (float)te, (float)ub);
-            }
+        const double Da = D_eval32(I, (float)aux[4 * q], (float)aux[4 * q + 1], (float)ua);
+        const double Db = D_eval32(I, (float)aux[4 * q + 2], (float)aux[4 * q + 3], (float)ub);
+        double fa = f_eval(I, xa, aux[4 * q], te, ua);   // sources keep FP64 (rarely used)
+        double fb = f_eval(I, xb, aux[4 * q + 2], te, ub);
+        if (I.fpar[4] == 0.0 && I.fpar[5] == 0.0) {
+            fa = f_eval32(I, (float)aux[4 * q], (float)te, (float)ua);
+            fb = f_eval32(I, (float)aux[4 * q + 2], (float)te, (float)ub);
         }
         ms.wpd[q] = df_from_double(w * (Da + Db));
         ms.wmd[q] = df_from_double(w * (Da - Db));

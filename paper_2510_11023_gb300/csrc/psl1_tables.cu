@@ -49,7 +49,8 @@ __global__ void k_gauss_legendre_half(int Q, double lo, double hi, double* xh, d
 // families at x_q and its mirror.
 __global__ void k_basis_tables(int Mx, int Qh, double lo, double hi, const double* xh, double* St,
                                double* S, double* C, double* aux, df* Std, df* Sd, df* Cd, double* Dt,
-                               df* Dtd, float* St32, float* Dt32, double* aux2)
+                               df* Dtd, float* St32, float* Dt32, double* aux2, const double* wh, df* Wd,
+                               df* auxd, df* aux2d)
 {
     int q = blockIdx.x;
     if (q >= Qh) return;
@@ -81,6 +82,10 @@ __global__ void k_basis_tables(int Mx, int Qh, double lo, double hi, const doubl
         aux[4 * q + 3] = sinpi(2.0 * xb);
         aux2[2 * q + 0] = cospi(2.0 * xa);
         aux2[2 * q + 1] = cospi(2.0 * xb);
+        for (int i = 0; i < 4; ++i) auxd[4 * q + i] = df_from_double(aux[4 * q + i]);
+        aux2d[2 * q + 0] = df_from_double(aux2[2 * q + 0]);
+        aux2d[2 * q + 1] = df_from_double(aux2[2 * q + 1]);
+        Wd[q] = df_from_double(wh[q]);
     }
 }
 
@@ -123,7 +128,8 @@ cudaError_t launch_tables(const TableJob& job, cudaStream_t s)
                                           job.aux, reinterpret_cast<df*>(job.Std), reinterpret_cast<df*>(job.Sd),
                                           reinterpret_cast<df*>(job.Cd), job.Dt, reinterpret_cast<df*>(job.Dtd),
                                           reinterpret_cast<float*>(job.St32), reinterpret_cast<float*>(job.Dt32),
-                                          job.aux2);
+                                          job.aux2, job.wh, reinterpret_cast<df*>(job.Wd),
+                                          reinterpret_cast<df*>(job.auxd), reinterpret_cast<df*>(job.aux2d));
     return cudaGetLastError();
 }
 
