@@ -92,7 +92,10 @@ __device__ __forceinline__ void df_columns(const df* A, int lda, int i0, int i1,
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int j = 0; j < D; ++j) tv[r][j] = col[r][(size_t)(i + j) * lda];
+            for (int j = 0; j < D; ++j) {   // read-only path: the tables are never written by the kernel
+                const float2 v = __ldg(reinterpret_cast<const float2*>(col[r] + (size_t)(i + j) * lda));
+                tv[r][j] = df{v.x, v.y};
+            }
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -462,7 +465,9 @@ __device__ void th_product32(int K, PcgSmem& cg)
     const int ng = (K + 3) / 4;
     int S = NT / ng;
     S = S < 1 ? 1 : (S > 16 ? 16 : S);
-    const int L = (K + S - 1) / S;
+    // odd chunk length: the S chunks of a warp start in different shared-memory
+    // banks (a multiple of 32 would put every chunk's loads in the same bank)
+    const int L = ((K + S - 1) / S) | 1;
     const int t = threadIdx.x;
     for (int task = t; task < ng * S; task += NT) {
         const int grp = task / S, c = task % S;
