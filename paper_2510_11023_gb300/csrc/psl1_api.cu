@@ -174,7 +174,7 @@ void psl1_destroy(psl1_h h)
 }
 
 // dpar / fpar as (hi, lo) float pairs for the double-float evaluation, and
-// whether f reduces to its polynomial term
+// whether f can be evaluated in double-float (no manufactured source)
 static void family_copies(InstDev& I)
 {
     for (int i = 0; i < 8; ++i) {
@@ -185,8 +185,7 @@ static void family_copies(InstDev& I)
         I.fpf[2 * i] = h;
         I.fpf[2 * i + 1] = (float)(I.fpar[i] - (double)h);
     }
-    const double* c = I.fpar;
-    I.f_poly = (c[0] == 0.0 && c[1] == 0.0 && c[3] == 0.0 && c[4] == 0.0 && c[5] == 0.0) ? 1 : 0;
+    I.f_df = (I.fpar[4] == 0.0 && I.fpar[5] == 0.0) ? 1 : 0;
 }
 
 static psl1_status validate(const psl1_instance& d, int P, int b)

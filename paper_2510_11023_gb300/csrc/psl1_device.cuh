@@ -41,7 +41,7 @@ struct InstDev {
     long long oW;                // offset in N*K fine-history pools (uniform solver)
     int Nb;                      // b(j) table length - 1 (max of N, P, m)
     int Qy, Qhy, tabY;           // y axis (2D): nodes, mirror pairs, table set
-    int f_poly;                  // f has only its polynomial term c2 u (1-u)
+    int f_df;                    // f has no manufactured source term (double-float evaluation)
     float dpf[16], fpf[16];      // dpar, fpar as double-float pairs (hi, lo)
 };
 

@@ -6,8 +6,8 @@
 // FP32 pipes: ~48-bit significands from error-free transformations (Knuth's
 // TwoSum, the FMA-exact product) and Newton-corrected division, with the
 // family parameters and node functions taken from double-float copies made
-// once (no FP64 operation per node).  Transcendental terms of f (cos u, sin u,
-// e^-t, the manufactured sources) stay FP64.
+// once (no FP64 operation per node).  cos u and sin u are evaluated in
+// double-float too (df_sincos); only the manufactured sources stay FP64.
 #pragma once
 #include "psl1_device.cuh"
 
@@ -88,10 +88,82 @@ __device__ __forceinline__ df D_eval_df(const InstDev& I, df sx1, df sx2, df cy2
     return df_mul(v, X0);
 }
 
-// the polynomial family of f (I.f_poly: only c2 u (1 - u) is active)
-__device__ __forceinline__ df f_poly_df(const InstDev& I, df u)
+// exact product a b = p + e
+__device__ __forceinline__ df two_prod(float a, float b)
 {
-    return df_mul(fpar_df(I, 2), df_mul(u, df_addn(df{1.f, 0.f}, df_neg(u))));
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// 1/n!, n = 0..17, as double-float pairs (hi = nearest float to 1/n!, lo =
+// nearest float to the remainder), written out from exact rational arithmetic.
+static __constant__ float kInvFact[18][2] = {
+    0x1.0000000000000p+0f, 0x0.0p+0f,   // 1/0!
+    0x1.0000000000000p+0f, 0x0.0p+0f,   // 1/1!
+    0x1.0000000000000p-1f, 0x0.0p+0f,   // 1/2!
+    0x1.5555560000000p-3f, -0x1.5555560000000p-28f,   // 1/3!
+    0x1.5555560000000p-5f, -0x1.5555560000000p-30f,   // 1/4!
+    0x1.1111120000000p-7f, -0x1.ddddde0000000p-32f,   // 1/5!
+    0x1.6c16c20000000p-10f, -0x1.27d27e0000000p-35f,   // 1/6!
+    0x1.a01a020000000p-13f, -0x1.7f97fa0000000p-39f,   // 1/7!
+    0x1.a01a020000000p-16f, -0x1.7f97fa0000000p-42f,   // 1/8!
+    0x1.71de3a0000000p-19f, 0x1.55b1cc0000000p-45f,   // 1/9!
+    0x1.27e4fc0000000p-22f, -0x1.10ec140000000p-47f,   // 1/10!
+    0x1.ae64560000000p-26f, 0x1.fd51380000000p-52f,   // 1/11!
+    0x1.1eed8e0000000p-29f, 0x1.ff1b120000000p-54f,   // 1/12!
+    0x1.6124620000000p-33f, -0x1.8af25e0000000p-58f,   // 1/13!
+    0x1.93974a0000000p-37f, 0x1.180f940000000p-62f,   // 1/14!
+    0x1.ae7f3e0000000p-41f, 0x1.ccee080000000p-67f,   // 1/15!
+    0x1.ae7f3e0000000p-45f, 0x1.ccee080000000p-71f,   // 1/16!
+    0x1.952c780000000p-49f, -0x1.f9ea560000000p-74f,   // 1/17!
+};
+
+__device__ __forceinline__ df inv_fact(int n) { return {kInvFact[n][0], kInvFact[n][1]}; }
+
+// sin u and cos u in double-float: Cody-Waite reduction u = n pi/2 + r with a
+// three-float split of pi/2 (each product n * part exact by FMA), then the
+// Taylor series of sin and cos on |r| <= pi/4, truncated after r^17 / 17! and
+// r^16 / 16! (next terms below 1e-17 there), summed by Horner in r^2.
+__device__ __forceinline__ void df_sincos(df u, df& sn, df& cs)
+{
+    constexpr double PIO2 = 1.5707963267948966;
+    constexpr float P1 = (float)PIO2;
+    constexpr float P2 = (float)(PIO2 - (double)P1);
+    constexpr float P3 = (float)(PIO2 - (double)P1 - (double)P2);
+    const float n = rintf(u.hi * 0.636619772f);   // nearest multiple of pi/2
+    df r = df_addn(u, df_neg(two_prod(n, P1)));
+    r = df_addn(r, df_neg(two_prod(n, P2)));
+    r = df_addn(r, df{-__fmul_rn(n, P3), 0.f});
+    const df r2 = df_mul(r, r);
+    df S = inv_fact(17), C = inv_fact(16);
+#pragma unroll
+    for (int j = 7; j >= 0; --j) {
+        const df a = inv_fact(2 * j + 1), b = inv_fact(2 * j);
+        S = df_addn((j & 1) ? df_neg(a) : a, df_mul(r2, S));
+        C = df_addn((j & 1) ? df_neg(b) : b, df_mul(r2, C));
+    }
+    // the j = 8 terms carry sign (+1): r^16/16! and r^17/17!
+    S = df_mul(r, S);
+    const int q = ((int)n) & 3;
+    const df s0 = S, c0 = C;
+    sn = q == 0 ? s0 : q == 1 ? c0 : q == 2 ? df_neg(s0) : df_neg(c0);
+    cs = q == 0 ? c0 : q == 1 ? df_neg(s0) : q == 2 ? df_neg(c0) : s0;
+}
+
+// f = c0 cos u + c1 sin u + c2 u (1 - u) + c3 sin(pi x) e^{-t} in double-float
+// (I.f_df: the manufactured sources c4, c5 are absent); emt = e^{-t} as double-float.
+__device__ __forceinline__ df f_eval_df(const InstDev& I, df sx1, df emt, df u)
+{
+    df v{0.f, 0.f};
+    if (I.fpar[0] != 0.0 || I.fpar[1] != 0.0) {
+        df sn, cs;
+        df_sincos(u, sn, cs);
+        if (I.fpar[0] != 0.0) v = df_addn(v, df_mul(fpar_df(I, 0), cs));
+        if (I.fpar[1] != 0.0) v = df_addn(v, df_mul(fpar_df(I, 1), sn));
+    }
+    if (I.fpar[2] != 0.0) v = df_addn(v, df_mul(fpar_df(I, 2), df_mul(u, df_addn(df{1.f, 0.f}, df_neg(u)))));
+    if (I.fpar[3] != 0.0) v = df_addn(v, df_mul(fpar_df(I, 3), df_mul(sx1, emt)));
+    return v;
 }
 
 }  // namespace psl1

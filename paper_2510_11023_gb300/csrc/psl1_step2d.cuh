@@ -589,6 +589,7 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
     for (int k = tid; k < K; k += NT) S.cdf[k] = df_from_double(c[k]);
     __syncthreads();
     to_nodes<NumDF, 2, 2>(g, td, S.cdf, T1, N1);
+    const df emt = (I.fpar[3] != 0.0 && !fp32_only) ? df_from_double(exp(-te)) : df{0.f, 0.f};
     for (int e = tid; e < QQ; e += NT) {
         const int i = e / g.Qy, j = e - i * g.Qy;
         if (fp32_only) {
@@ -601,13 +602,13 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
             N2[e] = df_from_double(wf);
             continue;
         }
-        // D (and a polynomial f) in double-float on the FP32 pipes; transcendental f in FP64
+        // D and f in double-float on the FP32 pipes (manufactured sources in FP64)
         const Node2df nd = node2_df(I, TX, TY, tp, i, j);
         const df u = N1[e];
         const df wD = df_mul(nd.w, D_eval_df(I, nd.sx1, nd.sx2, nd.cy2, u));
         df wf;
-        if (I.f_poly) {
-            wf = df_mul(nd.w, f_poly_df(I, u));
+        if (I.f_df) {
+            wf = df_mul(nd.w, f_eval_df(I, nd.sx1, emt, u));
         } else {
             const Node2 n64 = node2(I, TX, TY, tp, i, j);
             wf = df_from_double(n64.w * f_eval(I, n64.x, n64.sx1, te, df_to_double(u)));

@@ -186,16 +186,17 @@ __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const do
     __syncthreads();
     const df* wd = reinterpret_cast<const df*>(tp + Tb.oWd);
     const df* auxd = reinterpret_cast<const df*>(tp + Tb.oAuxd);
+    const df emt = (I.fpar[3] != 0.0 && !fp32_only) ? df_from_double(exp(-te)) : df{0.f, 0.f};
     for (int q = tid; q < Qh && !fp32_only; q += NT) {
-        // D (and a polynomial f) in double-float on the FP32 pipes; transcendental f in FP64
+        // D and f in double-float on the FP32 pipes (manufactured sources in FP64)
         const df o = ms.wpd[q], e = ms.wmd[q];
         const df ua = df_addn(o, e), ub = df_addn(o, df_neg(e));
         const df zero{0.f, 0.f};
         const df Da = D_eval_df(I, auxd[4 * q], auxd[4 * q + 1], zero, ua);
         const df Db = D_eval_df(I, auxd[4 * q + 2], auxd[4 * q + 3], zero, ub);
         df fs, fd;
-        if (I.f_poly) {
-            const df fa = f_poly_df(I, ua), fb = f_poly_df(I, ub);
+        if (I.f_df) {
+            const df fa = f_eval_df(I, auxd[4 * q], emt, ua), fb = f_eval_df(I, auxd[4 * q + 2], emt, ub);
             fs = df_addn(fa, fb);
             fd = df_addn(fa, df_neg(fb));
         } else {

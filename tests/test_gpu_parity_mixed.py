@@ -75,3 +75,19 @@ def test_mixed_finite_termination_bitwise():
         for j in range(k + 1):
             Uj = pr.get_iterate(j)[0]
             assert np.abs(Uj[: j + 1] - S[: j + 1]).max() <= 1e-13 * np.abs(S).max(), j
+
+
+@pytest.mark.parametrize("fpar", [(1.0,), (0, 1.0), (0.3, -0.2, 0.1, 0.5)])
+def test_mixed_step_dominated_by_f(fpar):
+    # hist = 0 and a large mu make the step ~ mu F(f(u)): the double-float
+    # evaluation of cos u, sin u (with u up to ~10, several multiples of pi/2)
+    # and of the other f terms is seen directly at the step tolerance
+    K = 40
+    spec = workloads.InstanceSpec(modes=(K, 1), nsteps=8, alpha=0.5, dpar=workloads.D_CFG2, fpar=fpar)
+    rng = np.random.default_rng(11)
+    c = 6.0 * rng.standard_normal(K) / np.arange(1, K + 1)
+    with psl1.Problem([spec], 2, precision="mixed") as pr:
+        for te, mu in ((0.3, 0.5), (1.7, 2.0)):
+            g = pr.step(0, c, te, mu, np.zeros(K))
+            o = O.step(oracle_prob(spec, 2), c, te, mu, np.zeros(K))
+            assert rel(g, o) < TOL_STEP["mixed"], (fpar, te, mu, rel(g, o))
