@@ -43,7 +43,7 @@ struct psl1_problem {
     std::vector<void*> allocs;
     InstDev* d_inst = nullptr;
     TabDev* d_tab = nullptr;
-    double *d_tp = nullptr, *d_bp = nullptr, *d_u0 = nullptr;
+    double *d_tp = nullptr, *d_bp = nullptr, *d_bpd = nullptr, *d_dud = nullptr, *d_u0 = nullptr;
     double *d_Ua = nullptr, *d_Ub = nullptr, *d_Us = nullptr, *d_Fv = nullptr, *d_Gold = nullptr;
     double *d_incr = nullptr, *d_work = nullptr, *d_ring = nullptr;
     int *d_nfirst = nullptr, *d_active = nullptr, *d_counter = nullptr;
@@ -402,6 +402,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     CTRY(dalloc(h, &h->d_tab, h->tabs.size()));
     CTRY(dalloc(h, &h->d_tp, h->tabElems));
     CTRY(dalloc(h, &h->d_bp, h->sumB));
+    CTRY(dalloc(h, &h->d_bpd, h->sumB));   // double-float pairs, 8 bytes each
     CTRY(dalloc(h, &h->d_u0, h->sumK));
     CTRY(dalloc(h, &h->d_Ua, h->sumU));
     CTRY(dalloc(h, &h->d_Ub, h->sumU));
@@ -422,6 +423,9 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     long long ring_stride = (long long)h->mmax * h->Kmax;
     CTRY(dalloc(h, &h->d_work, (size_t)nslots * work_stride));
     CTRY(dalloc(h, &h->d_ring, (size_t)nslots * ring_stride));
+    // mixed-path coarse differences (double-float, 8 bytes per entry)
+    long long dud_stride = precision == PSL1_PREC_FP64 ? 0 : (long long)P * h->Kmax;
+    if (dud_stride) CTRY(dalloc(h, &h->d_dud, (size_t)nslots * dud_stride));
     // fine units, longest first (cost ~ m K^3)
     std::vector<int2> units;
     for (int b = 0; b < batch; ++b)
@@ -469,7 +473,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
                             h->stream), "copy units"));
     CTRY(cu(cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream), "status"));
     for (auto& j : jobs) CTRY(cu(launch_tables(j, h->stream), "table kernels"));
-    CTRY(cu(launch_weights(h->d_inst, batch, h->d_bp, h->stream), "weight kernel"));
+    CTRY(cu(launch_weights(h->d_inst, batch, h->d_bp, h->d_bpd, h->stream), "weight kernel"));
     // constants computed on the device (mu, muT, ...) are needed on the host copy too
     CTRY(cu(cudaMemcpyAsync(h->inst.data(), h->d_inst, sizeof(InstDev) * batch, cudaMemcpyDeviceToHost, h->stream),
             "read constants"));
@@ -481,6 +485,9 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.tab = h->d_tab;
     a.tp = h->d_tp;
     a.bp = h->d_bp;
+    a.bpd = reinterpret_cast<const df*>(h->d_bpd);
+    a.dud = reinterpret_cast<df*>(h->d_dud);
+    a.dud_stride = dud_stride;
     a.status = h->d_status;
     a.work = h->d_work;
     a.work_stride = work_stride;
@@ -970,13 +977,14 @@ psl1_status psl1_fine_slice_noalloc(psl1_h h, int b, int n, const double* d_U, d
                      : h->prec == PSL1_PREC_FP64 ? bp_elems(I.nb, TILE)
                      : (h->pa.fac_in_smem || h->pa.inner == INNER_PCG) ? 0
                                                 : (bp_elems(I.nb, MIX_LDB) + 1) / 2;
-    if (ring + work > NOALLOC_SCRATCH_DOUBLES)
+    long long dud = h->prec == PSL1_PREC_FP64 ? 0 : (long long)(n + 1) * I.K;   // coarse differences
+    if (ring + work + dud > NOALLOC_SCRATCH_DOUBLES)
         return fail(h, PSL1_ERR_ARG,
-                    "instance %d needs %lld doubles of scratch (m*K = %lld plus factor %lld); the fixed "
-                    "allocation-free array holds %lld",
-                    b, ring + work, ring, work, NOALLOC_SCRATCH_DOUBLES);
+                    "instance %d needs %lld doubles of scratch (m*K = %lld, factor %lld, coarse differences "
+                    "%lld); the fixed allocation-free array holds %lld",
+                    b, ring + work + dud, ring, work, dud, NOALLOC_SCRATCH_DOUBLES);
     TRY(reset_status(h));
-    CU(h, launch_one_slice_noalloc(h->pa, b, n, d_U, d_V, ring, work, h->stream));
+    CU(h, launch_one_slice_noalloc(h->pa, b, n, d_U, d_V, ring, work, dud, h->stream));
     return check_device_status(h);
 }
 

@@ -303,13 +303,48 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
     const int K = I.K, m = I.m, tid = threadIdx.x;
     const double* bF = a.bp + I.oB;
     const double* bC = bF + I.Nb + 1;
+    // FP32-pipe paths: the history sums accumulate in double-float, the coarse
+    // differences U_i - U_{i-1} are formed once per slice, and the ring holds
+    // the fine differences as double-float pairs
+    const bool dfh = a.prec != 0;
+    const df* bFd = a.bpd + I.oB;
+    const df* bCd = bFd + I.Nb + 1;
+    df* dud = a.dud + (size_t)blockIdx.x * a.dud_stride;
+    df* ringd = reinterpret_cast<df*>(ring);
     for (int k = tid; k < K; k += NT) {
         cv.cur[k] = U[(size_t)n * K + k];
         if (Vout) Vout[k] = cv.cur[k];
     }
+    if (dfh)
+        for (int e = tid; e < n * K; e += NT) dud[e] = df_from_double(U[e + K] - U[e]);
     __syncthreads();
     for (int r = 1; r <= m; ++r) {
-        for (int k = tid; k < K; k += NT) {
+        for (int k = tid; k < K && dfh; k += NT) {
+            // four independent partial sums (the loads of a term do not wait on the previous one)
+            dfacc a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+            int j = 1;
+            for (; j + 3 <= r - 1; j += 4) {
+                dfacc_fma(a0, bFd[r - j], ringd[(size_t)(j - 1) * K + k]);
+                dfacc_fma(a1, bFd[r - j - 1], ringd[(size_t)j * K + k]);
+                dfacc_fma(a2, bFd[r - j - 2], ringd[(size_t)(j + 1) * K + k]);
+                dfacc_fma(a3, bFd[r - j - 3], ringd[(size_t)(j + 2) * K + k]);
+            }
+            for (; j <= r - 1; ++j) dfacc_fma(a0, bFd[r - j], ringd[(size_t)(j - 1) * K + k]);
+            const df* bc = bCd + (r - 1);
+            int i = 1;
+            for (; i + 3 <= n; i += 4) {
+                dfacc_fma(a0, bc[(size_t)(n - i) * m], dud[(size_t)(i - 1) * K + k]);
+                dfacc_fma(a1, bc[(size_t)(n - i - 1) * m], dud[(size_t)i * K + k]);
+                dfacc_fma(a2, bc[(size_t)(n - i - 2) * m], dud[(size_t)(i + 1) * K + k]);
+                dfacc_fma(a3, bc[(size_t)(n - i - 3) * m], dud[(size_t)(i + 2) * K + k]);
+            }
+            for (; i <= n; ++i) dfacc_fma(a0, bc[(size_t)(n - i) * m], dud[(size_t)(i - 1) * K + k]);
+            dfacc_add(a0, dfacc_result(a1));
+            dfacc_add(a2, dfacc_result(a3));
+            dfacc_add(a0, dfacc_result(a2));
+            cv.hist[k] = cv.cur[k] - df_to_double(dfacc_result(a0));
+        }
+        for (int k = tid; k < K && !dfh; k += NT) {
             double h = cv.cur[k];
             for (int j = 1; j <= r - 1; ++j) h -= bF[r - j] * ring[(size_t)(j - 1) * K + k];
             const double* bc = bC + (r - 1);
@@ -323,7 +358,10 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
         if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_FINE, n * m + r);
         check_finite(a, cv.nxt, K, ii, WHERE_FINE, n * m + r);
         for (int k = tid; k < K; k += NT) {
-            ring[(size_t)(r - 1) * K + k] = cv.nxt[k] - cv.cur[k];
+            if (dfh)
+                ringd[(size_t)(r - 1) * K + k] = df_from_double(cv.nxt[k] - cv.cur[k]);
+            else
+                ring[(size_t)(r - 1) * K + k] = cv.nxt[k] - cv.cur[k];
             cv.cur[k] = cv.nxt[k];
             if (Vout) Vout[(size_t)r * K + k] = cv.nxt[k];
         }
@@ -775,7 +813,8 @@ double* g_noalloc_addr[kMaxDevices] = {};
 }  // namespace
 
 cudaError_t launch_one_slice_noalloc(const PathArgs& a, int b, int n, const double* U, double* V,
-                                     long long ring_doubles, long long work_doubles, cudaStream_t s)
+                                     long long ring_doubles, long long work_doubles, long long dud_doubles,
+                                     cudaStream_t s)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -792,6 +831,8 @@ cudaError_t launch_one_slice_noalloc(const PathArgs& a, int b, int n, const doub
     a2.ring_stride = ring_doubles;
     a2.work = g_noalloc_addr[dev] + ring_doubles;
     a2.work_stride = work_doubles;
+    a2.dud = reinterpret_cast<df*>(g_noalloc_addr[dev] + ring_doubles + work_doubles);
+    a2.dud_stride = dud_doubles;
     a2.nslots = 1;
     size_t sm = step_smem_bytes(a2);
     return a.dim2 ? launch_k(k_one_slice_noalloc<true>, 1, sm, s, a2, b, n, U, V)

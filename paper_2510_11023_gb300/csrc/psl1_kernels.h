@@ -49,6 +49,9 @@ struct PathArgs {
     const TabDev* tab;
     const double* tp;        // table pool
     const double* bp;        // L1 weight pool
+    const df* bpd;           // the same weights as double-float (mixed history sums)
+    df* dud;                 // per-CTA-slot coarse differences U_i - U_{i-1} (P x Kmax, double-float)
+    long long dud_stride;
     DevStatus* status;
     double* work;            // per-CTA-slot matrix workspace (FP64 factor)
     long long work_stride;   // doubles per slot
@@ -72,7 +75,7 @@ SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int 
 size_t step_smem_bytes(const PathArgs& a);
 
 cudaError_t launch_tables(const TableJob& job, cudaStream_t s);
-cudaError_t launch_weights(InstDev* inst, int B, double* bpool, cudaStream_t s);
+cudaError_t launch_weights(InstDev* inst, int B, double* bpool, double* bpool_df, cudaStream_t s);
 
 // Parareal pieces.
 cudaError_t launch_fstage(const PathArgs& a, const double* Uold, double* Fv, const int2* units, int nunits,
@@ -114,6 +117,7 @@ cudaError_t launch_pr_update(const double* incr, int* active, int* nfirst, int* 
 // Single slice with scratch from a fixed device array (no allocation).
 constexpr long long NOALLOC_SCRATCH_DOUBLES = 512 * 1024;   // 4 MiB
 cudaError_t launch_one_slice_noalloc(const PathArgs& a, int b, int n, const double* U, double* V,
-                                     long long ring_doubles, long long work_doubles, cudaStream_t s);
+                                     long long ring_doubles, long long work_doubles, long long dud_doubles,
+                                     cudaStream_t s);
 
 }  // namespace psl1

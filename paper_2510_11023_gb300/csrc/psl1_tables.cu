@@ -97,7 +97,7 @@ __device__ __forceinline__ double l1w(double a, double x)
 }
 
 // Per-instance constants and weight tables.  One CTA per instance.
-__global__ void k_weights(InstDev* inst, double* bpool)
+__global__ void k_weights(InstDev* inst, double* bpool, df* bpool_df)
 {
     InstDev& I = inst[blockIdx.x];
     double a = I.alpha;
@@ -112,11 +112,17 @@ __global__ void k_weights(InstDev* inst, double* bpool)
     double ma = pow((double)I.m, -a);
     double* bF = bpool + I.oB;
     double* bC = bF + I.Nb + 1;
-    for (int j = threadIdx.x; j <= I.Nb; j += blockDim.x) bF[j] = l1w(a, (double)j);
+    df* bFd = bpool_df + I.oB;
+    df* bCd = bFd + I.Nb + 1;
+    for (int j = threadIdx.x; j <= I.Nb; j += blockDim.x) {
+        bF[j] = l1w(a, (double)j);
+        bFd[j] = df_from_double(bF[j]);
+    }
     // bC[d*m + (r-1)] = m^-a b(d + r/m)
     for (int e = threadIdx.x; e < I.P * I.m; e += blockDim.x) {
         int d = e / I.m, r = e % I.m + 1;
         bC[e] = ma * l1w(a, (double)d + (double)r / I.m);
+        bCd[e] = df_from_double(bC[e]);
     }
 }
 
@@ -133,9 +139,9 @@ cudaError_t launch_tables(const TableJob& job, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_weights(InstDev* inst, int B, double* bpool, cudaStream_t s)
+cudaError_t launch_weights(InstDev* inst, int B, double* bpool, double* bpool_df, cudaStream_t s)
 {
-    k_weights<<<B, 256, 0, s>>>(inst, bpool);
+    k_weights<<<B, 256, 0, s>>>(inst, bpool, reinterpret_cast<df*>(bpool_df));
     return cudaGetLastError();
 }
 
