@@ -53,7 +53,7 @@ struct psl1_problem {
     double* d_flops = nullptr;   // algorithmic FLOP accumulators: F stage, coarse, serial, pieces
     // uniform solver pools (lazy)
     double *d_Wcur = nullptr, *d_dW = nullptr, *d_part = nullptr;
-    int uni_chunk = 256, uni_maxchunks = 0;
+    int uni_chunk = 32, uni_maxchunks = 0;   // history rows per CTA of k_uni_hist
     cudaGraphExec_t uni_graph = nullptr;   // the uniform solver's N-step launch sequence
     // graph-mode parareal (device-driven while loop)
     bool graph_mode = false;

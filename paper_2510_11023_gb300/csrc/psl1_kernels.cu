@@ -643,8 +643,14 @@ __global__ void k_uni_init(const InstDev* inst, const double* u0, double* Wcur, 
 // Partial history sums of the uniform scheme at step j (computing W_{j+1}):
 //   part[c][k] = sum_{l in chunk c} b_{j-l} dW_l[k],  dW_l = W_{l+1} - W_l.
 // Reads each history row once per step; coalesced along modes.
-__global__ void __launch_bounds__(NT) k_uni_hist(const InstDev* inst, const double* bp, const double* dW, int j,
-                                                 double* part, int chunk, int maxchunks, int Kmax)
+// DF: the FP32-pipe paths store the fine differences as double-float and sum
+// them in double-float (the FP64 pipe would bound the stream); FP64 path in FP64.
+// Each thread keeps eight rows in flight (four partial sums) so that the stream
+// is bound by HBM, not by one load at a time.
+template <bool DF>
+__global__ void __launch_bounds__(NT) k_uni_hist(const InstDev* inst, const double* bp, const df* bpd,
+                                                 const double* dW, int j, double* part, int chunk, int maxchunks,
+                                                 int Kmax)
 {
     const int ii = blockIdx.y, c = blockIdx.x;
     const InstDev& I = inst[ii];
@@ -652,13 +658,53 @@ __global__ void __launch_bounds__(NT) k_uni_hist(const InstDev* inst, const doub
     const int l0 = c * chunk;
     if (l0 >= j) return;
     const int l1 = min(j, l0 + chunk);
-    const double* bF = bp + I.oB;
-    const double* h = dW + I.oW;
+    const size_t K = I.K;
     double* out = part + ((size_t)ii * maxchunks + c) * Kmax;
     for (int k = threadIdx.x; k < I.K; k += NT) {
-        double acc = 0.0;
-        for (int l = l0; l < l1; ++l) acc = fma(bF[j - l], h[(size_t)l * I.K + k], acc);
-        out[k] = acc;
+        if constexpr (DF) {
+            const df* w = bpd + I.oB;
+            const df* h = reinterpret_cast<const df*>(dW + I.oW) + k;
+            dfacc a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+            int l = l0;
+            for (; l + 8 <= l1; l += 8) {
+                df v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = h[(size_t)(l + q) * K];
+                dfacc_fma(a0, w[j - l], v[0]);
+                dfacc_fma(a1, w[j - l - 1], v[1]);
+                dfacc_fma(a2, w[j - l - 2], v[2]);
+                dfacc_fma(a3, w[j - l - 3], v[3]);
+                dfacc_fma(a0, w[j - l - 4], v[4]);
+                dfacc_fma(a1, w[j - l - 5], v[5]);
+                dfacc_fma(a2, w[j - l - 6], v[6]);
+                dfacc_fma(a3, w[j - l - 7], v[7]);
+            }
+            for (; l < l1; ++l) dfacc_fma(a0, w[j - l], h[(size_t)l * K]);
+            dfacc_add(a0, dfacc_result(a1));
+            dfacc_add(a2, dfacc_result(a3));
+            dfacc_add(a0, dfacc_result(a2));
+            out[k] = df_to_double(dfacc_result(a0));
+        } else {
+            const double* bF = bp + I.oB;
+            const double* h = dW + I.oW + k;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int l = l0;
+            for (; l + 8 <= l1; l += 8) {
+                double v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = h[(size_t)(l + q) * K];
+                a0 = fma(bF[j - l], v[0], a0);
+                a1 = fma(bF[j - l - 1], v[1], a1);
+                a2 = fma(bF[j - l - 2], v[2], a2);
+                a3 = fma(bF[j - l - 3], v[3], a3);
+                a0 = fma(bF[j - l - 4], v[4], a0);
+                a1 = fma(bF[j - l - 5], v[5], a1);
+                a2 = fma(bF[j - l - 6], v[6], a2);
+                a3 = fma(bF[j - l - 7], v[7], a3);
+            }
+            for (; l < l1; ++l) a0 = fma(bF[j - l], h[(size_t)l * K], a0);
+            out[k] = (a0 + a1) + (a2 + a3);
+        }
     }
 }
 
@@ -686,7 +732,10 @@ k_uni_step(PathArgs a, double* Wcur, double* dW, double* Us, int j, const double
     const bool node = ((j + 1) % I.m) == 0;
     for (int k = tid; k < K; k += NT) {
         double x = cv.nxt[k];
-        dW[I.oW + (size_t)j * K + k] = x - cv.cur[k];
+        if (a.prec == 0)
+            dW[I.oW + (size_t)j * K + k] = x - cv.cur[k];
+        else   // double-float differences for the FP32-pipe history sums
+            reinterpret_cast<df*>(dW + I.oW)[(size_t)j * K + k] = df_from_double(x - cv.cur[k]);
         Wcur[I.oK + k] = x;
         if (node) Us[I.oU + (size_t)((j + 1) / I.m) * K + k] = x;
     }
@@ -876,7 +925,10 @@ cudaError_t launch_uni_hist(const PathArgs& a, int B, const double* dW, int j, d
     int nch = (j + chunk - 1) / chunk;
     if (nch <= 0) return cudaSuccess;
     dim3 grid(nch, B);
-    k_uni_hist<<<grid, NT, 0, s>>>(a.inst, a.bp, dW, j, part, chunk, maxchunks, a.Kmax);
+    if (a.prec == 0)
+        k_uni_hist<false><<<grid, NT, 0, s>>>(a.inst, a.bp, a.bpd, dW, j, part, chunk, maxchunks, a.Kmax);
+    else
+        k_uni_hist<true><<<grid, NT, 0, s>>>(a.inst, a.bp, a.bpd, dW, j, part, chunk, maxchunks, a.Kmax);
     return cudaGetLastError();
 }
 
