@@ -165,3 +165,25 @@ def test_learned_correction_rejected_for_2d():
         with pytest.raises(psl1.PSL1Error) as ei:
             pr.set_coarse(m)
         assert ei.value.status == -1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_2d_error_paths(prec):
+    # D = -1 makes I + mu A indefinite: conjugate gradients meets p . (I + mu A) p <= 0
+    # (PSL1_ERR_NOT_SPD) or the iterate blows up (PSL1_ERR_NONFINITE); either way the solve
+    # reports the failure, and the handle stays usable with a valid D
+    wl = workloads.small_batch_2d()
+    with psl1.Problem(wl, precision=prec) as pr:
+        good = np.concatenate([np.asarray(s.dpar + (0,) * (8 - len(s.dpar)), dtype=np.float64) for s in wl.specs])
+        bad = good.copy()
+        bad[0::8] = -1.0
+        bad[1::8] = 0.0
+        pr.set_D(bad)
+        with pytest.raises(psl1.PSL1Error) as ei:
+            pr.solve_serial("hybrid")
+        assert ei.value.status in (-2, -3)
+        pr.set_D(good)
+        pr.solve_serial("hybrid")
+        S = pr.get_coeffs("serial")
+    for b, spec in enumerate(wl.specs):
+        assert rel(S[b], O.serial_hyb(oracle_prob(spec, wl.P), wl.u0[b])) < TOL
