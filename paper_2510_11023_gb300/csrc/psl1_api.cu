@@ -382,8 +382,6 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     int nslots = std::max(2 * h->nsm, batch);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int fac_in_smem = 0;
-    const int inner = INNER_PCG;
     const bool two_d = in[0].dim == 2;
     SmemLayout lay{};
     Layout2D lay2{};
@@ -391,7 +389,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         lay2 = make_layout2d(precision, h->Kmax, nT2, nN2, ntab2, max_smem - 1024);
         lay.total = lay2.smem;
     } else {
-        lay = make_layout(precision, inner, h->Kmax, h->Kpmax, h->Qhmax, max_smem - 1024, &fac_in_smem);
+        lay = make_layout(precision, h->Kmax, h->Kpmax, h->Qhmax);
     }
     if (lay.total > max_smem - 1024) {
         g_create_error = "instance too large for the shared-memory layout";
@@ -418,8 +416,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     // per-slot factor workspace: FP64 factor, or the FP32 factor when it does not fit in shared memory
     long long work_stride = two_d ? std::max(1LL, (lay2.gbytes + 255) / 256 * 32)   // 256-byte aligned slots
                             : precision == PSL1_PREC_FP64 ? bp_elems(nbmax, TILE)
-                            : (fac_in_smem || inner == INNER_PCG) ? 1
-                                                         : (bp_elems(nbmax, MIX_LDB) + 1) / 2;
+                            : 1;
     long long ring_stride = (long long)h->mmax * h->Kmax;
     CTRY(dalloc(h, &h->d_work, (size_t)nslots * work_stride));
     CTRY(dalloc(h, &h->d_ring, (size_t)nslots * ring_stride));
@@ -500,8 +497,6 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.mmax = h->mmax;
     a.prec = precision;
     a.L = lay;
-    a.fac_in_smem = fac_in_smem;
-    a.inner = inner;
     a.flops = h->d_flops;
     a.flop_slot = 3;
     a.dim2 = two_d ? 1 : 0;
@@ -975,8 +970,7 @@ psl1_status psl1_fine_slice_noalloc(psl1_h h, int b, int n, const double* d_U, d
     long long ring = (long long)I.m * I.K;
     long long work = h->pa.dim2 ? h->pa.work_stride   // 2D working arrays outside shared memory
                      : h->prec == PSL1_PREC_FP64 ? bp_elems(I.nb, TILE)
-                     : (h->pa.fac_in_smem || h->pa.inner == INNER_PCG) ? 0
-                                                : (bp_elems(I.nb, MIX_LDB) + 1) / 2;
+                     : 0;
     long long dud = h->prec == PSL1_PREC_FP64 ? 0 : (long long)(n + 1) * I.K;   // coarse differences
     if (ring + work + dud > NOALLOC_SCRATCH_DOUBLES)
         return fail(h, PSL1_ERR_ARG,

@@ -17,9 +17,6 @@ constexpr int NT = 256;          // threads per CTA of the step kernels
 constexpr int KMAX_1D = 512;     // largest 1D mode count handled by one CTA
 constexpr int MMAX_2D = 64;      // largest 2D mode count per axis (K = Mx My <= 4096)
 constexpr int TILE = 32;         // Cholesky block size (one warp per panel)
-constexpr int INNER_CHOL = 0;    // FP32 inner solver of the refinement: blocked Cholesky
-constexpr int INNER_PCG = 1;     //                                      Jacobi-preconditioned CG
-constexpr int MIX_LDB = 33;      // padded row stride of FP32 factor blocks (bank-conflict free)
 
 // elements of a block-packed lower triangle of nb x nb blocks with row stride ldb
 __host__ __device__ constexpr int bp_elems(int nb, int ldb) { return nb * (nb + 1) / 2 * TILE * ldb; }

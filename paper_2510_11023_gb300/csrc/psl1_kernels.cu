@@ -22,7 +22,6 @@ struct Carve {
     StepSmem s;
     MixSmem ms;
     PcgSmem cg;
-    float* fac;
     df *mz, *mh0, *mh1;      // learned-correction features and hidden activations (double-float)
     Step2D s2;               // 2D working arrays
 };
@@ -113,14 +112,11 @@ __device__ __forceinline__ Carve carve(const PathArgs& a, char* base)
     c.mz = at<df>(base, L.mz);
     c.mh0 = at<df>(base, L.mh0);
     c.mh1 = at<df>(base, L.mh1);
-    c.fac = a.fac_in_smem ? at<float>(base, L.fac)
-                          : reinterpret_cast<float*>(a.work + (size_t)blockIdx.x * a.work_stride);
     return c;
 }
 
-// Shared-memory layout.  Regions are 16-byte aligned; the FP32 factor goes
-// last and is placed in shared memory only if the whole layout fits.
-SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem)
+// Shared-memory layout of the 1D step kernels.  Regions are 16-byte aligned.
+SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax)
 {
     SmemLayout L;
     int off = 0;
@@ -152,7 +148,7 @@ SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int 
     L.rhs = f64 ? -1 : take(8 * (size_t)Kpmax);
     L.z = f64 ? -1 : take(4 * (size_t)Kpmax);
     L.red = f64 ? -1 : take(4 * (NT / 32));
-    const bool pcg = !f64 && inner == INNER_PCG;
+    const bool pcg = !f64;   // CG inner solver of the FP32-pipe paths
     L.cgx = pcg ? take(4 * (size_t)Kpmax) : -1;
     L.cgr = pcg ? take(4 * (size_t)Kpmax) : -1;
     L.cgp = pcg ? take(4 * (size_t)Kpmax) : -1;
@@ -167,15 +163,6 @@ SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int 
     L.mz = take(8 * (size_t)MLP_MAX_IN);
     L.mh0 = take(8 * (size_t)MLP_MAX_WIDTH);
     L.mh1 = take(8 * (size_t)MLP_MAX_WIDTH);
-    L.fac = -1;
-    *fac_in_smem = 0;
-    if (!f64 && !pcg) {
-        size_t fb = 4 * (size_t)bp_elems(Kpmax / TILE, MIX_LDB);
-        if (off + fb <= (size_t)max_smem) {
-            L.fac = take(fb);
-            *fac_in_smem = 1;
-        }
-    }
     L.total = off;
     return L;
 }
@@ -264,9 +251,7 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
             BPack<double, TILE> A{a.work + (size_t)blockIdx.x * a.work_stride};
             bad = step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
         } else {
-            BPack<float, MIX_LDB> A{cv.fac};
-            bad = step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s, cv.ms, cv.cg, a.prec == 2,
-                             a.inner);
+            bad = step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, cv.s, cv.ms, cv.cg, a.prec == 2);
         }
         // algorithmic FLOPs of the step: transforms (u, moments, load: 4 K^2 multiply-adds with
         // Q = 2K nodes), coefficient evaluation (~30 per node), and the solve -- FP64: Cholesky
@@ -278,7 +263,7 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
             if (a.prec == 0)
                 f += K * K2 / 3.0 + 2.0 * K2;
             else
-                f += 4.0 * K2 * (cv.s.bad[1] + cv.s.bad[2]) + (a.inner == INNER_CHOL ? K * K2 / 3.0 : 0.0);
+                f += 4.0 * K2 * (cv.s.bad[1] + cv.s.bad[2]);
             atomicAdd(a.flops + a.flop_slot, f);
         }
         return bad;

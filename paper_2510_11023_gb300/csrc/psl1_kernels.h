@@ -19,7 +19,7 @@ struct TableJob {
 // Byte offsets of the per-CTA shared-memory regions (host-computed; -1 = absent).
 struct SmemLayout {
     int cur, hist, nxt, F, v, wp, wm, fp, fm, g, bad;     // FP64 path (+ common)
-    int cdf, wpd, wmd, fpd, fmd, gdf, ydf, x, rhs, z, red, fac;   // FP32-pipe path
+    int cdf, wpd, wmd, fpd, fmd, gdf, ydf, x, rhs, z, red;   // FP32-pipe path
     int cgx, cgr, cgp, cgq, cgpl, cgdinv, cgred, cggs, cggh, cgpart;   // PCG inner solver
     int mpart;                                                   // split-transform partial sums
     int mz, mh0, mh1;                                            // learned correction inference
@@ -53,7 +53,7 @@ struct PathArgs {
     df* dud;                 // per-CTA-slot coarse differences U_i - U_{i-1} (P x Kmax, double-float)
     long long dud_stride;
     DevStatus* status;
-    double* work;            // per-CTA-slot matrix workspace (FP64 factor)
+    double* work;            // per-CTA-slot workspace (FP64 factor; 2D arrays outside shared memory)
     long long work_stride;   // doubles per slot
     double* ring;            // per-CTA-slot fine history ring (m x K doubles)
     long long ring_stride;
@@ -61,8 +61,6 @@ struct PathArgs {
     int Kmax, Kpmax, Qhmax, mmax;
     int prec;                // PSL1_PREC_*
     SmemLayout L;            // shared-memory layout of the step kernels
-    int fac_in_smem;         // FP32 factor in shared memory (else in the work slot)
-    int inner;               // INNER_CHOL or INNER_PCG (FP32-pipe paths)
     double* flops;           // algorithmic FLOP accumulators (by slot), may be null
     int flop_slot;           // 0 F stage, 1 coarse sweeps, 2 serial solvers, 3 single pieces
     MlpDev mlp;              // learned coarse correction (mlp.on = 0: plain L1 G)
@@ -70,7 +68,7 @@ struct PathArgs {
     Layout2D L2;
 };
 
-SmemLayout make_layout(int prec, int inner, int Kmax, int Kpmax, int Qhmax, int max_smem, int* fac_in_smem);
+SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax);
 
 size_t step_smem_bytes(const PathArgs& a);
 

@@ -5,10 +5,11 @@
 //   * mode -> node transform, quadrature moments g_s and the load vector are
 //     accumulated in double-float (unevaluated FP32 pairs, ~48-bit
 //     significand) from double-float tables;
-//   * D and f are evaluated in FP64 at the nodes (Q evaluations per step);
-//   * the inner solver works on the FP32 operator I + mu cA k l (g_|k-l| + g_{k+l}):
-//     Jacobi-preconditioned CG (default), or an FP32 Cholesky factor
-//     (block-packed lower storage in shared memory when it fits);
+//   * D and f are evaluated in double-float at the nodes (psl1_dfmath.cuh; the
+//     manufactured sources in FP64);
+//   * the inner solver is Jacobi-preconditioned CG on the FP32 operator
+//     I + mu cA k l (g_|k-l| + g_{k+l}) (an FP32 blocked Cholesky factor was
+//     measured 3.7x slower at K = 256 and is not used);
 //   * iterative refinement: r = rhs - M x with M applied in double-float
 //     through the Toeplitz+Hankel form, z = M32^{-1} r in FP32, x += z, until
 //     max|z| <= 1e-11 max|x|, or until the contraction of the last two
@@ -242,200 +243,6 @@ __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const do
     __syncthreads();
 }
 
-// FP32 matrix from the moments (hi parts), identity padding.
-__device__ void fill_matrix32(const InstDev& I, const df* g, double mu, BPack<float, MIX_LDB> A)
-{
-    const int nb = I.nb, K = I.K;
-    const int total = nb * (nb + 1) / 2 * TILE * TILE;
-    const float sc = (float)(mu * I.cA);
-    for (int e = threadIdx.x; e < total; e += NT) {
-        int bidx = e >> 10, w = e & 1023, i = w >> 5, j = w & 31;
-        int a = (int)((sqrtf(8.0f * bidx + 1.0f) - 1.0f) * 0.5f);
-        while ((a + 1) * (a + 2) / 2 <= bidx) ++a;
-        while (a * (a + 1) / 2 > bidx) --a;
-        int Jb = bidx - a * (a + 1) / 2;
-        int k = TILE * a + i, l = TILE * Jb + j;
-        float val;
-        if (k < K && l < K) {
-            int d = k > l ? k - l : l - k;
-            val = (k == l ? 1.0f : 0.0f) + sc * (float)((k + 1) * (l + 1)) * (g[d].hi + g[k + l + 2].hi);
-        } else {
-            val = (k == l) ? 1.0f : 0.0f;
-        }
-        A.blk(a, Jb)[i * MIX_LDB + j] = val;
-    }
-    __syncthreads();
-}
-
-// ------------------------------------------------------------------ FP32 factor with inverted diagonal blocks
-// Right-looking blocked Cholesky whose diagonal blocks end up holding
-// inv(L_JJ) instead of L_JJ: the panel solve becomes a row-parallel product
-// and each diagonal triangular solve a 32-wide matrix-vector product, so only
-// the 32-column factorisation of a diagonal block is sequential.
-
-// Warp-cooperative: factor the 32x32 block D (row stride MIX_LDB) and
-// overwrite it with inv(L).  Lane i holds row i in registers.
-__device__ __forceinline__ void diag_factor_inv32(float* D, int J, int* bad)
-{
-    const int lane = threadIdx.x & 31;
-    float a[TILE];
-#pragma unroll
-    for (int p = 0; p < TILE; ++p) a[p] = p <= lane ? D[lane * MIX_LDB + p] : 0.f;
-#pragma unroll
-    for (int j = 0; j < TILE; ++j) {
-        float piv = __shfl_sync(0xffffffffu, a[j], j);
-        if (!(piv > 0.f)) {
-            if (lane == 0 && *bad < 0) *bad = TILE * J + j;
-            piv = 1.f;
-        }
-        float d = sqrtf(piv), rd = 1.0f / d;
-        if (lane == j) a[j] = d;
-        if (lane > j) a[j] *= rd;
-#pragma unroll
-        for (int k = j + 1; k < TILE; ++k) {
-            float lkj = __shfl_sync(0xffffffffu, a[j], k);
-            if (lane >= k) a[k] -= a[j] * lkj;
-        }
-    }
-    // L to shared memory, then lane c computes column c of inv(L) by forward substitution
-#pragma unroll
-    for (int p = 0; p < TILE; ++p)
-        if (p <= lane) D[lane * MIX_LDB + p] = a[p];
-    __syncwarp();
-    float x[TILE];
-#pragma unroll
-    for (int i = 0; i < TILE; ++i) {
-        float s = (i == lane) ? 1.f : 0.f;
-#pragma unroll
-        for (int p = 0; p < i; ++p) s -= D[i * MIX_LDB + p] * x[p];
-        x[i] = (i >= lane) ? s / D[i * MIX_LDB + i] : 0.f;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < TILE; ++i)
-        if (i >= lane) D[i * MIX_LDB + lane] = x[i];
-    __syncwarp();
-}
-
-__device__ void chol32_factor_inv(BPack<float, MIX_LDB> A, int nb, int* bad)
-{
-    const int tid = threadIdx.x, warp = tid >> 5;
-    for (int J = 0; J < nb; ++J) {
-        if (warp == 0) diag_factor_inv32(A.blk(J, J), J, bad);
-        __syncthreads();
-        // panel: L_IJ = A_IJ inv(L_JJ)^T, one row per thread, in place
-        const float* Li = A.blk(J, J);
-        const int nrows = (nb - J - 1) * TILE;
-        for (int rr = tid; rr < nrows; rr += NT) {
-            float* row = A.blk(J + 1 + rr / TILE, J) + (rr % TILE) * MIX_LDB;
-            float in[TILE], out[TILE];
-#pragma unroll
-            for (int p = 0; p < TILE; ++p) {
-                in[p] = row[p];
-                out[p] = 0.f;
-            }
-#pragma unroll
-            for (int c = 0; c < TILE; ++c)
-#pragma unroll
-                for (int p = 0; p <= c; ++p) out[c] += in[p] * Li[c * MIX_LDB + p];
-#pragma unroll
-            for (int p = 0; p < TILE; ++p) row[p] = out[p];
-        }
-        __syncthreads();
-        const int nrem = nb - J - 1;
-        const int ntiles = nrem * (nrem + 1) / 2 * 64;
-        for (int t = tid; t < ntiles; t += NT) {
-            int pr = t >> 6, tt = t & 63;
-            int a = (int)((sqrtf(8.0f * pr + 1.0f) - 1.0f) * 0.5f);
-            while ((a + 1) * (a + 2) / 2 <= pr) ++a;
-            while (a * (a + 1) / 2 > pr) --a;
-            int b = pr - a * (a + 1) / 2;
-            int I = J + 1 + a, I2 = J + 1 + b;
-            int ti = tt >> 3, tj = tt & 7;
-            if (I == I2 && tj > ti) continue;
-            const float* La = A.blk(I, J) + (4 * ti) * MIX_LDB;
-            const float* Lb = A.blk(I2, J) + (4 * tj) * MIX_LDB;
-            float acc[4][4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
-#pragma unroll 8
-            for (int p = 0; p < TILE; ++p) {
-                float x[4], y[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    x[r] = La[r * MIX_LDB + p];
-                    y[r] = Lb[r * MIX_LDB + p];
-                }
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(x[r], y[c], acc[r][c]);
-            }
-            float* C = A.blk(I, I2) + (4 * ti) * MIX_LDB + 4 * tj;
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) C[r * MIX_LDB + c] -= acc[r][c];
-        }
-        __syncthreads();
-    }
-}
-
-// Solve L L^T x = v in place with the factor of chol32_factor_inv.  Every warp
-// forms the 32 diagonal-block results itself (a 32-term product per lane), so
-// one barrier per block suffices; the block's results are stored one block later.
-__device__ void chol32_solve_inv(BPack<float, MIX_LDB> A, int nb, float* v)
-{
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    float ylast = 0.f;
-    for (int J = 0; J < nb; ++J) {
-        const float* Li = A.blk(J, J);
-        float y = 0.f;
-#pragma unroll
-        for (int p = 0; p < TILE; ++p)
-            if (p <= lane) y += Li[lane * MIX_LDB + p] * v[TILE * J + p];
-        if (J > 0 && warp == 0) v[TILE * (J - 1) + lane] = ylast;
-        ylast = y;
-        const int nrows = (nb - J - 1) * TILE;
-        for (int rb = warp * 32; rb < nrows; rb += NT) {   // warp-uniform row blocks
-            int rr = rb + lane;
-            float s = 0.f;
-            const float* row = A.blk(J + 1 + rr / TILE, J) + (rr % TILE) * MIX_LDB;
-#pragma unroll
-            for (int p = 0; p < TILE; ++p) s += row[p] * __shfl_sync(0xffffffffu, y, p);
-            v[TILE * (J + 1) + rr] -= s;
-        }
-        __syncthreads();
-    }
-    if (warp == 0) v[TILE * (nb - 1) + lane] = ylast;
-    __syncthreads();
-    float xlast = 0.f;
-    for (int J = nb - 1; J >= 0; --J) {
-        const float* Li = A.blk(J, J);
-        float x = 0.f;
-#pragma unroll
-        for (int p = 0; p < TILE; ++p)
-            if (p >= lane) x += Li[p * MIX_LDB + lane] * v[TILE * J + p];
-        if (J < nb - 1 && warp == 0) v[TILE * (J + 1) + lane] = xlast;
-        xlast = x;
-        const int ncols = J * TILE;
-        for (int cb = warp * 32; cb < ncols; cb += NT) {
-            int cc = cb + lane;
-            const float* blk = A.blk(J, cc / TILE);
-            int c = cc % TILE;
-            float s = 0.f;
-#pragma unroll
-            for (int r = 0; r < TILE; ++r) s += blk[r * MIX_LDB + c] * __shfl_sync(0xffffffffu, x, r);
-            v[cc] -= s;
-        }
-        __syncthreads();
-    }
-    if (warp == 0) v[lane] = xlast;
-    __syncthreads();
-}
-
 // ------------------------------------------------------------------ FP32 PCG inner solver
 // z = M^{-1} r approximately, M = I + mu cA k l (g_|k-l| + g_{k+l}) applied in
 // FP32 from the moments' hi parts, Jacobi preconditioner.  For
@@ -636,13 +443,11 @@ __device__ void residual_df(const InstDev& I, double mu, MixSmem& ms)
 
 // The step: c (K, shared) -> out (K, shared).  Returns the first bad pivot or -1.
 __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, const double* c,
-                          const double* hist, double te, double mu, double* out, double* F,
-                          BPack<float, MIX_LDB> A, StepSmem& s, MixSmem& ms, PcgSmem& cg, bool fp32_only,
-                          int inner)
+                          const double* hist, double te, double mu, double* out, double* F, StepSmem& s,
+                          MixSmem& ms, PcgSmem& cg, bool fp32_only)
 {
     const int tid = threadIdx.x;
     nodes_moments_mixed(I, Tb, tp, c, te, ms, F, fp32_only);
-    if (inner == INNER_CHOL) fill_matrix32(I, ms.gdf, mu, A);
     // refinement from x = 0: the first correction is the FP32 solve of rhs
     for (int k = tid; k < I.Kp; k += NT) {
         double r = k < I.K ? hist[k] + mu * F[k] : 0.0;
@@ -652,12 +457,7 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
     }
     if (tid == 0) *s.bad = -1;
     __syncthreads();
-    if (inner == INNER_CHOL) {
-        chol32_factor_inv(A, I.nb, s.bad);
-        chol32_solve_inv(A, I.nb, ms.z);
-    } else {
-        pcg32(I, mu, ms, cg, PCG_MAXIT, PCG_RTOL);
-    }
+    pcg32(I, mu, ms, cg, PCG_MAXIT, PCG_RTOL);
     float zprev = 0.f;
     for (int sweep = 0;; ++sweep) {
         float zmax = 0.f, xmax = 0.f;
@@ -676,10 +476,7 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
         zprev = zmax;
         if (tid == 0) ms.flag[2] += 1;
         residual_df(I, mu, ms);
-        if (inner == INNER_CHOL)
-            chol32_solve_inv(A, I.nb, ms.z);
-        else
-            pcg32(I, mu, ms, cg, PCG_MAXIT, PCG_RTOL);
+        pcg32(I, mu, ms, cg, PCG_MAXIT, PCG_RTOL);
     }
     for (int k = tid; k < I.K; k += NT) out[k] = ms.x[k];
     __syncthreads();
