@@ -133,7 +133,10 @@ psl1_status psl1_set_u0(psl1_h h, const double* coeffs);
 psl1_status psl1_set_u0_dev(psl1_h h, const double* d_coeffs);
 
 /* Serial solve of every instance (kind: PSL1_SERIAL_*).  The result at the
- * coarse nodes is kept in the "serial" slot (see psl1_get_coeffs).          */
+ * coarse nodes is kept in the "serial" slot (see psl1_get_coeffs).  The first
+ * UNIFORM solve of a handle also autotunes the history stream (row chunk per
+ * CTA, timed on the longest history launch) and captures the N-step launch
+ * sequence into a CUDA graph that later UNIFORM solves replay.              */
 psl1_status psl1_solve_serial(psl1_h h, int kind);
 
 /* Parareal iteration (Eq. Parareal with the stored G_old of the flowchart):

@@ -53,7 +53,7 @@ struct psl1_problem {
     double* d_flops = nullptr;   // algorithmic FLOP accumulators: F stage, coarse, serial, pieces
     // uniform solver pools (lazy)
     double *d_Wcur = nullptr, *d_dW = nullptr, *d_part = nullptr;
-    int uni_chunk = 32, uni_maxchunks = 0;   // history rows per CTA of k_uni_hist
+    int uni_chunk = 32, uni_maxchunks = 0;   // history rows per CTA of k_uni_hist (autotuned)
     cudaGraphExec_t uni_graph = nullptr;   // the uniform solver's N-step launch sequence
     // graph-mode parareal (device-driven while loop)
     bool graph_mode = false;
@@ -553,13 +553,47 @@ psl1_status psl1_set_u0_dev(psl1_h h, const double* c)
     return PSL1_OK;
 }
 
+// candidate row chunks of the history stream (k_uni_hist), smallest first
+static const int kUniChunks[] = {16, 32, 64, 128};
+
 static psl1_status ensure_uniform_pools(psl1_problem* h)
 {
     if (h->d_dW) return PSL1_OK;
-    h->uni_maxchunks = (h->Nmax + h->uni_chunk - 1) / h->uni_chunk;
+    h->uni_maxchunks = (h->Nmax + kUniChunks[0] - 1) / kUniChunks[0];   // room for any candidate
     TRY(dalloc(h, &h->d_Wcur, h->sumK));
     TRY(dalloc(h, &h->d_dW, h->sumNK));
     TRY(dalloc(h, &h->d_part, (size_t)h->B * h->uni_maxchunks * h->Kmax));
+    CU(h, cudaMemsetAsync(h->d_dW, 0, sizeof(double) * h->sumNK, h->stream));
+    return PSL1_OK;
+}
+
+// Autotuning of the history stream: its row chunk sets the grid (chunks x
+// instances CTAs) and so how much of HBM's latency is covered; the best value
+// depends on the batch, K and N.  Every candidate is timed on the longest
+// history launch (fine step Nmax - 1) after one warm-up launch, and the fastest
+// is kept for the handle (the sums differ only in their association order).
+static psl1_status tune_uniform_chunk(psl1_problem* h)
+{
+    const int j = h->Nmax - 1;
+    if (j < 2) return PSL1_OK;
+    float best = 0.f;
+    int pick = h->uni_chunk;
+    bool first = true;
+    for (int c : kUniChunks) {
+        CU(h, launch_uni_hist(h->pa, h->B, h->d_dW, j, h->d_part, c, h->uni_maxchunks, h->stream));
+        CU(h, cudaEventRecord(h->ev[2], h->stream));
+        CU(h, launch_uni_hist(h->pa, h->B, h->d_dW, j, h->d_part, c, h->uni_maxchunks, h->stream));
+        CU(h, cudaEventRecord(h->ev[3], h->stream));
+        CU(h, cudaEventSynchronize(h->ev[3]));
+        float ms = 0.f;
+        CU(h, cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
+        if (first || ms < best) {
+            best = ms;
+            pick = c;
+            first = false;
+        }
+    }
+    h->uni_chunk = pick;
     return PSL1_OK;
 }
 
@@ -622,6 +656,8 @@ psl1_status psl1_solve_serial(psl1_h h, int kind)
         // replayed afterwards: every argument is a fixed pool or a step index, and
         // u0, D and f are read from device memory when the graph runs.
         if (!h->uni_graph) {
+            TRY(tune_uniform_chunk(h));
+            CU(h, cudaEventRecord(h->ev[0], h->stream));   // the timed solve starts after the tuning
             cudaGraph_t g = nullptr;
             CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = enqueue_uniform(h);
