@@ -27,8 +27,6 @@
 
 namespace psl1 {
 
-
-
 struct MixSmem {
     df* cdf;      // K   : c as double-float
     df* wpd;      // Qh  : w (D_q + D_q')  (double-float)
@@ -428,13 +426,21 @@ __device__ void residual_df(const InstDev& I, double mu, MixSmem& ms)
     __syncthreads();
     const double sc = mu * I.cA;
     for (int k = tid; k < K; k += NT) {
-        dfacc a1{0.f, 0.f}, a2{0.f, 0.f};
-        for (int l = 0; l < K; ++l) {
-            int d = k > l ? k - l : l - k;
-            dfacc_fma(a1, ms.gdf[d], ms.ydf[l]);
-            dfacc_fma(a2, ms.gdf[k + l + 2], ms.ydf[l]);
+        // (g_|k-l| + g_{k+l+2}) y_l: the Toeplitz and Hankel entries are added first
+        // (one double-float multiply-add per entry), in two independent partial sums
+        dfacc a0{0.f, 0.f}, a1{0.f, 0.f};
+        int l = 0;
+        for (; l + 1 < K; l += 2) {
+            const int d0 = k > l ? k - l : l - k, d1 = k > l + 1 ? k - l - 1 : l + 1 - k;
+            dfacc_fma(a0, df_add(ms.gdf[d0], ms.gdf[k + l + 2]), ms.ydf[l]);
+            dfacc_fma(a1, df_add(ms.gdf[d1], ms.gdf[k + l + 3]), ms.ydf[l + 1]);
         }
-        double s = df_to_double(dfacc_result(a1)) + df_to_double(dfacc_result(a2));
+        if (l < K) {
+            const int d0 = k > l ? k - l : l - k;
+            dfacc_fma(a0, df_add(ms.gdf[d0], ms.gdf[k + l + 2]), ms.ydf[l]);
+        }
+        dfacc_add(a0, dfacc_result(a1));
+        const double s = df_to_double(dfacc_result(a0));
         ms.z[k] = (float)(ms.rhs[k] - ms.x[k] - sc * (double)(k + 1) * s);   // residual, FP32 for the solve
     }
     for (int k = K + tid; k < I.Kp; k += NT) ms.z[k] = 0.f;

@@ -187,3 +187,19 @@ def test_2d_error_paths(prec):
         S = pr.get_coeffs("serial")
     for b, spec in enumerate(wl.specs):
         assert rel(S[b], O.serial_hyb(oracle_prob(spec, wl.P), wl.u0[b])) < TOL
+
+
+def test_full_size_64x64_parareal_reaches_serial_solution():
+    # one instance of the 2D batched workload at its full size (64 x 64 modes,
+    # 128 x 128 nodes, N = 8192, P = 256; node arrays in the slot workspace):
+    # parareal converges to S_hyb, its fixed point (Eq. PararealConvergence)
+    wl = workloads.cfg5(B=1)
+    with psl1.Problem(wl, precision="mixed") as pr:
+        pr.set_graph(True)
+        k = pr.solve_parareal(tol=1e-10)
+        U = pr.get_coeffs("parareal")[0]
+        pr.solve_serial("hybrid")
+        S = pr.get_coeffs("serial")[0]
+    assert 1 <= k < wl.P
+    assert rel(U, S) < 1e-9, rel(U, S)
+    assert np.all(np.isfinite(S)) and np.abs(S).max() > 0
