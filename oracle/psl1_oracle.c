@@ -22,8 +22,8 @@
  *   Sec. 2.2, Eq. (Parareal), Fig. (parareal) parareal iteration, stored G_old
  *   Sec. 2.2, Eq. (PararealConvergence)       fixed point = sequential F sweep
  * Readings where the paper is silent (sine basis, exact identity mass matrix,
- * stopping quantity, learned coarse propagator) are listed in the design doc of
- * the repository and restated at each function below.
+ * stopping quantity, learned coarse propagator) are stated at each function
+ * below where they apply.
  *
  * Parity status: every function here is pinned by a -m "not gpu" test
  * (closed forms, invariants, brute force, library routines) except the
