@@ -178,6 +178,21 @@ psl1_status psl1_get_iterate(psl1_h h, int k, double* out);
  * No counterpart in the paper (its iteration is the same, Fig. parareal).     */
 psl1_status psl1_set_graph(psl1_h h, int on);
 
+/* Inexact early parareal iterations (off by default, above = 0).  With
+ * above > 0, the F stage of iteration k runs the slices n > k with one FP32
+ * inner solve per fine step instead of the refined solve, as long as the
+ * instance's last increment e_{k-1} exceeds `above` (and always at k = 0);
+ * slice n = k, which starts from exact states, keeps the refined solve.  The
+ * fixed point (the sequential F sweep S_hyb) and the exactness of
+ * U^{k+1}_{0:k+1} are unchanged; the cheaper early F stages perturb the
+ * iterate by about the FP32 solve's error, which the later, refined
+ * iterations remove, so `above` should stay well above that (1e-4 is used by
+ * the benchmark).  Affects MIXED 1D instances only; a no-op for FP64, FP32
+ * and 2D.  Rebuilds the parareal graph.  PSL1_ERR_ARG for negative or
+ * non-finite values.  No counterpart in the paper (an implementation choice:
+ * its iteration, Eq. Parareal, uses the same F throughout).                 */
+psl1_status psl1_set_inexact_fine(psl1_h h, double above);
+
 /* Statistics of the last solve.                                             */
 psl1_status psl1_get_stats(psl1_h h, psl1_stats* st);
 

@@ -501,6 +501,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.flop_slot = 3;
     a.dim2 = two_d ? 1 : 0;
     a.L2 = lay2;
+    a.incr = h->d_incr;
+    a.loose_above = 0.0;
     h->iters.assign(batch, 0);
     h->errlog.assign(batch, {});
     h->d_Ucur = h->d_Ua;
@@ -1375,6 +1377,18 @@ psl1_status psl1_mlp_train(psl1_mlp_h mh, psl1_h data, int epochs, int batch, fl
         }
     }
     MCU(mh, cudaStreamSynchronize(mh->stream));
+    return PSL1_OK;
+}
+
+psl1_status psl1_set_inexact_fine(psl1_h h, double above)
+{
+    if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
+    if (!(above >= 0.0) || !std::isfinite(above)) return fail(h, PSL1_ERR_ARG, "threshold must be finite and >= 0");
+    h->pa.loose_above = above;
+    if (h->par_graph) {   // the graph holds the kernels' arguments
+        cudaGraphExecDestroy(h->par_graph);
+        h->par_graph = nullptr;
+    }
     return PSL1_OK;
 }
 

@@ -222,7 +222,8 @@ enum { WHERE_FINE = 1, WHERE_COARSE = 2, WHERE_UNI = 3, WHERE_ONE = 4 };
 
 template <bool D2>
 __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, const double* c,
-                                       const double* hist, double te, double mu, double* out, Carve& cv)
+                                       const double* hist, double te, double mu, double* out, Carve& cv,
+                                       bool one_solve = false)
 {
     const TabDev& Tb = a.tab[I.tab];
     int bad;
@@ -251,7 +252,7 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
             BPack<double, TILE> A{a.work + (size_t)blockIdx.x * a.work_stride};
             bad = step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
         } else {
-            bad = step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, cv.s, cv.ms, cv.cg, a.prec == 2);
+            bad = step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, cv.s, cv.ms, cv.cg, a.prec == 2, one_solve);
         }
         // algorithmic FLOPs of the step: transforms (u, moments, load: 4 K^2 multiply-adds with
         // Q = 2K nodes), coefficient evaluation (~30 per node), and the solve -- FP64: Cholesky
@@ -282,7 +283,7 @@ __device__ __forceinline__ void check_finite(const PathArgs& a, const double* v,
 // m^-a sum_{i=1}^n b(n-i+r/m) (U_i - U_{i-1})  (Eq. L1Fine, difference form).
 template <bool D2>
 __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, double* Vout, double* out,
-                           Carve& cv, double* ring)
+                           Carve& cv, double* ring, bool one_solve = false)
 {
     const InstDev& I = a.inst[ii];
     const int K = I.K, m = I.m, tid = threadIdx.x;
@@ -339,7 +340,7 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
         }
         if (tid == 0 && a.flops) atomicAdd(a.flops + a.flop_slot, 2.0 * K * (r - 1 + n));
         __syncthreads();
-        int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n + I.dt * (r - 1), I.mu, cv.nxt, cv);
+        int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n + I.dt * (r - 1), I.mu, cv.nxt, cv, one_solve);
         if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_FINE, n * m + r);
         check_finite(a, cv.nxt, K, ii, WHERE_FINE, n * m + r);
         for (int k = tid; k < K; k += NT) {
@@ -521,7 +522,13 @@ k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nuni
         const int ii = units[u].x, n = units[u].y;
         if (!active[ii] || n < nfirst[ii]) continue;
         const InstDev& I = a.inst[ii];
-        fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring);
+        // Inexact early iterations (opt-in): while the last increment is large, the
+        // slices after the first one still in error take one FP32 solve per step.
+        // Slice n = nfirst starts from exact states and stays exact, so U^{k+1}_{k+1}
+        // and the fixed point are unchanged.  At k = 0 no increment exists yet.
+        const bool one_solve = a.loose_above > 0.0 && n > nfirst[ii] &&
+                               (nfirst[ii] == 0 || a.incr[ii] > a.loose_above);
+        fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring, one_solve);
     }
 }
 

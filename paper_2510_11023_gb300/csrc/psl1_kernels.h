@@ -66,6 +66,8 @@ struct PathArgs {
     MlpDev mlp;              // learned coarse correction (mlp.on = 0: plain L1 G)
     int dim2;                // 2D instances (the 2D layout below applies)
     Layout2D L2;
+    const double* incr;      // last parareal increment e_k per instance (written by the correction sweep)
+    double loose_above;      // > 0: inexact F stage while e_k > loose_above (1D MIXED only; 0: off)
 };
 
 SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax);

@@ -448,9 +448,12 @@ __device__ void residual_df(const InstDev& I, double mu, MixSmem& ms)
 }
 
 // The step: c (K, shared) -> out (K, shared).  Returns the first bad pivot or -1.
+// one_solve: stop after the first FP32 solve (no refinement; D, f and the
+// transforms stay double-float) -- the inexact fine steps of early parareal
+// iterations.
 __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, const double* c,
                           const double* hist, double te, double mu, double* out, double* F, StepSmem& s,
-                          MixSmem& ms, PcgSmem& cg, bool fp32_only)
+                          MixSmem& ms, PcgSmem& cg, bool fp32_only, bool one_solve = false)
 {
     const int tid = threadIdx.x;
     nodes_moments_mixed(I, Tb, tp, c, te, ms, F, fp32_only);
@@ -478,7 +481,7 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
         xmax = block_max(xmax, ms.red);
         const bool small = zmax <= REFINE_TOL * xmax;
         const bool predicted = sweep >= 1 && zmax < zprev && zmax * zmax <= REFINE_EST * xmax * zprev;
-        if (fp32_only || small || predicted || sweep >= 6 || *s.bad >= 0) break;
+        if (fp32_only || one_solve || small || predicted || sweep >= 6 || *s.bad >= 0) break;
         zprev = zmax;
         if (tid == 0) ms.flag[2] += 1;
         residual_df(I, mu, ms);

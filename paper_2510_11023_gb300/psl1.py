@@ -69,6 +69,7 @@ SIGNATURES = {
     "psl1_get_errlog": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_int, _I]),
     "psl1_keep_iterates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "psl1_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "psl1_set_inexact_fine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "psl1_get_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D]),
     "psl1_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "psl1_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, _D, _D]),
@@ -261,6 +262,11 @@ class Problem:
     def set_graph(self, on: bool = True):
         """Run parareal as one CUDA graph with a device-driven iteration loop."""
         _chk(self.L.psl1_set_graph(self.h, int(on)), self.h)
+
+    def set_inexact_fine(self, above: float):
+        """Inexact early iterations: one FP32 solve per fine step on slices n > k
+        while the last increment exceeds `above` (0: off).  MIXED 1D only."""
+        _chk(self.L.psl1_set_inexact_fine(self.h, float(above)), self.h)
 
     def get_iterate(self, k: int) -> list:
         out = np.zeros(int(self.offU[-1]))

@@ -43,6 +43,7 @@ def test_invalid_arguments_rejected_before_device_use():
     bad.alpha = 1.5
     arr = (psl1.Instance * 1)(bad)
     assert L.psl1_create(ctypes.byref(h), 1, arr, 8, 0, None) == -1
+    assert L.psl1_set_inexact_fine(None, 1e-4) == -1
 
 
 def test_invalid_2d_arguments_rejected_before_device_use():

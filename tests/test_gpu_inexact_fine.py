@@ -1,0 +1,90 @@
+"""Inexact early parareal iterations (psl1_set_inexact_fine, MIXED 1D).
+
+While an instance's last increment is above the threshold, the F stage of
+iteration k runs slices n > k with one FP32 inner solve per fine step; slice
+n = k starts from exact states and keeps the refined solve.  Parareal's
+properties must survive (Eq. PararealConvergence): after k iterations the
+states U^k_{0:k} equal the sequential F sweep S_hyb, the iteration still ends
+at S_hyb, and graph mode reproduces the host loop bitwise.  Tolerances are
+those of the mixed path: 1e-13 relative for the exact prefix (as in the
+finite-termination test of the refined path), 1e-10 for whole solves."""
+import numpy as np
+import pytest
+
+from paper_2510_11023_gb300 import psl1, workloads
+from helpers import rel
+
+pytestmark = pytest.mark.gpu
+TOL_SOLVE = 1e-10
+
+
+def _batch():
+    return workloads.cfg2(B=6, seed=77, P=16, kmin=32, kmax=96, mmin=4, mmax=12)
+
+
+def test_exact_prefix_and_fixed_point_with_every_early_slice_inexact():
+    # a threshold of 1e-300 keeps every slice n > k inexact in every iteration:
+    # only the exactness of slice n = k carries the iteration to S_hyb
+    wl = workloads.cfg1(K=48, N=96, P=6)
+    with psl1.Problem(wl, precision="mixed") as pr:
+        pr.solve_serial("hybrid")
+        S = pr.get_coeffs("serial")[0]
+        pr.set_inexact_fine(1e-300)
+        pr.keep_iterates(True)
+        k = pr.solve_parareal(tol=0.0)
+        assert k == wl.P
+        for j in range(k + 1):
+            Uj = pr.get_iterate(j)[0]
+            assert np.abs(Uj[: j + 1] - S[: j + 1]).max() <= 1e-13 * np.abs(S).max(), j
+        assert rel(pr.get_coeffs("parareal")[0], S) <= 1e-13
+
+
+def test_inexact_early_iterations_converge_to_serial_with_less_fine_work():
+    wl = _batch()
+    with psl1.Problem(wl, precision="mixed") as pr:
+        pr.solve_serial("hybrid")
+        S = pr.get_coeffs("serial")
+        k0 = pr.solve_parareal(tol=1e-12)
+        U0 = pr.get_coeffs("parareal")
+        f0 = pr.stats()["flop_fine"]
+        pr.set_inexact_fine(1e-4)
+        k1 = pr.solve_parareal(tol=1e-12)
+        U1 = pr.get_coeffs("parareal")
+        f1 = pr.stats()["flop_fine"]
+        pr.set_inexact_fine(0.0)          # off again: the refined iteration, bitwise
+        k2 = pr.solve_parareal(tol=1e-12)
+        U2 = pr.get_coeffs("parareal")
+    for b in range(wl.B):
+        assert rel(U0[b], S[b]) < TOL_SOLVE, b
+        assert rel(U1[b], S[b]) < TOL_SOLVE, (b, rel(U1[b], S[b]))
+        assert np.array_equal(U2[b], U0[b]), b
+    assert k2 == k0
+    assert k1 <= k0 + 1, (k0, k1)
+    if k1 == k0:
+        assert f1 < f0, (f0, f1)
+
+
+def test_inexact_graph_mode_equals_host_loop():
+    wl = _batch()
+    out = []
+    for graph in (False, True):
+        with psl1.Problem(wl, precision="mixed") as pr:
+            pr.set_inexact_fine(1e-4)
+            pr.set_graph(graph)
+            pr.solve_parareal(tol=1e-11, allow_not_converged=True)
+            out.append((pr.get_coeffs("parareal", flat=True), pr.get_iterations(),
+                        [pr.get_errlog(b) for b in range(wl.B)]))
+    (Uh, ih, lh), (Ug, ig, lg) = out
+    assert np.array_equal(ih, ig)
+    assert np.array_equal(Uh, Ug)
+    for a, b in zip(lh, lg):
+        assert np.array_equal(a, b)
+
+
+def test_inexact_threshold_rejects_bad_values():
+    wl = workloads.cfg1(K=8, N=16, P=4)
+    with psl1.Problem(wl, precision="mixed") as pr:
+        for bad in (-1.0, float("nan"), float("inf")):
+            with pytest.raises(psl1.PSL1Error) as ei:
+                pr.set_inexact_fine(bad)
+            assert ei.value.status == -1
