@@ -64,8 +64,8 @@ typedef enum {
  *  MIXED: FP32-pair ("double-float") transforms and residuals, an FP32 inner
  *         solver (conjugate gradients) inside iterative refinement against
  *         the FP64-accurate operator.
- *  FP32 : FP32 coefficient functions and a single FP32 inner solve; no
- *         refinement.                                                       */
+ *  FP32 : FP32 coefficient functions, a single FP32 inner solve and no
+ *         refinement; 1D transforms in FP32 from FP32 tables.               */
 enum { PSL1_PREC_FP64 = 0, PSL1_PREC_MIXED = 1, PSL1_PREC_FP32 = 2 };
 
 /* Serial solvers.
@@ -179,13 +179,14 @@ psl1_status psl1_get_iterate(psl1_h h, int k, double* out);
 psl1_status psl1_set_graph(psl1_h h, int on);
 
 /* Inexact early parareal iterations (off by default, above = 0).  With
- * above > 0, the F stage of iteration k runs the slices n > k with one FP32
- * inner solve per fine step instead of the refined solve, as long as the
- * instance's last increment e_{k-1} exceeds `above` (and always at k = 0);
- * slice n = k, which starts from exact states, keeps the refined solve.  The
- * fixed point (the sequential F sweep S_hyb) and the exactness of
- * U^{k+1}_{0:k+1} are unchanged; the cheaper early F stages perturb the
- * iterate by about the FP32 solve's error, which the later, refined
+ * above > 0, the F stage of iteration k runs the slices n > k with the FP32
+ * step of PSL1_PREC_FP32 (FP32 transforms, D and f, one FP32 inner solve)
+ * instead of the refined step, as long as the instance's last increment
+ * e_{k-1} exceeds `above` (and always at k = 0); slice n = k, which starts
+ * from exact states, keeps the refined step.  The fixed point (the
+ * sequential F sweep S_hyb) and the exactness of U^{k+1}_{0:k+1} are
+ * unchanged; the cheaper early F stages perturb the iterate by about the
+ * FP32 step's error (~1e-6 relative), which the later, refined
  * iterations remove, so `above` should stay well above that (1e-4 is used by
  * the benchmark).  Affects MIXED 1D instances only; a no-op for FP64, FP32
  * and 2D.  Rebuilds the parareal graph.  PSL1_ERR_ARG for negative or

@@ -306,6 +306,10 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         o += 4LL * t.Qh;
         t.oAux2d = o;
         o += 2LL * t.Qh;
+        t.oS32 = o;
+        o += (mq + 1) / 2;
+        t.oC32 = o;
+        o += ((long long)t.Qh * (2 * t.Mx + 1) + 1) / 2;
         h->tabElems = o;
         int id = (int)h->tabs.size();
         h->tabs.push_back(t);
@@ -457,6 +461,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         jobs[t].Wd = h->d_tp + T.oWd;
         jobs[t].auxd = h->d_tp + T.oAuxd;
         jobs[t].aux2d = h->d_tp + T.oAux2d;
+        jobs[t].S32 = h->d_tp + T.oS32;
+        jobs[t].C32 = h->d_tp + T.oC32;
     }
     auto cu = [&](cudaError_t e2, const char* what) -> psl1_status {
         if (e2 != cudaSuccess) return fail(h, PSL1_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e2));

@@ -56,6 +56,7 @@ struct TabDev {
     long long oSt32, oDt32;   // Mx x Qh FP32 copies of St and Dt (two floats per slot)
     long long oAux2; // 2*Qh: cos(2 pi x) at x_q and at the mirror node
     long long oWd, oAuxd, oAux2d;   // Qh weights, 4*Qh aux, 2*Qh aux2 as double-float pairs
+    long long oS32, oC32;   // FP32 copies of S (Qh x Mx) and C (Qh x (2Mx+1)), packed floats
 };
 
 // Device error word: the first failure wins.  code < 0 is a psl1_status.

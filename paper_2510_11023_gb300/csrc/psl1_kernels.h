@@ -14,6 +14,7 @@ struct TableJob {
     double *Std, *Sd, *Cd;   // double-float copies (float pairs stored in 8-byte slots)
     double *Dt, *Dtd, *St32, *Dt32, *aux2;   // derivative table, FP32 copies, cos(2 pi x)
     double *Wd, *auxd, *aux2d;               // double-float copies of the weights and node functions
+    double *S32, *C32;                       // FP32 copies of S and C (packed floats)
 };
 
 // Byte offsets of the per-CTA shared-memory regions (host-computed; -1 = absent).

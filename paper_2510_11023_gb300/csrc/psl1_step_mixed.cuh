@@ -16,11 +16,10 @@
 //     corrections puts the next one below 1e-13 max|x| (at most 6 sweeps).
 //     The FP32 solver is only a preconditioner; the fixed point is the
 //     solution of the FP64-accurate system.
-// PSL1_PREC_FP32 runs the same kernel with D and f evaluated in FP32 and a
-// single FP32 solve (no refinement).  Its transforms stay double-float: a
-// plain FP32 moment loop was found to produce wrong moments under ptxas -O3
-// whenever one thread accumulates more than one moment (correct at -O1 and
-// in double-float), so that loop form is not used.
+// PSL1_PREC_FP32 runs the same kernel as an FP32 step: the three transforms
+// from FP32 table copies with FP32 accumulation (f32_transform), D and f in
+// FP32, and a single FP32 solve (no refinement).  The inexact early fine steps
+// of parareal (psl1_set_inexact_fine) are this FP32 step.
 #pragma once
 #include "psl1_step.cuh"
 #include "psl1_dfmath.cuh"
@@ -168,7 +167,83 @@ __device__ void df_transform(const df* A, int lda, int n, int nout, const df* x0
     __syncthreads();
 }
 
-// nodes + moments + load.  fp32_only: D and f in FP32.
+// FP32 rows i0..i1-1 of one output column: a0 (+)= sum A[i][o] x[i].hi, with
+// odd rows into a1 when TWO; i0 is even, so a row's parity is that of j.
+template <bool TWO>
+__device__ __forceinline__ void f32_rows(const float* col, int lda, int i0, int i1, const df* x, float& a0,
+                                         float& a1)
+{
+    int i = i0;
+    for (; i + 8 <= i1; i += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __ldg(col + (size_t)(i + j) * lda);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (TWO && (j & 1))
+                a1 = fmaf(v[j], x[i + j].hi, a1);
+            else
+                a0 = fmaf(v[j], x[i + j].hi, a0);
+        }
+    }
+    for (; i < i1; ++i) {
+        const float v = __ldg(col + (size_t)i * lda);
+        if (TWO && (i & 1))
+            a1 = fmaf(v, x[i].hi, a1);
+        else
+            a0 = fmaf(v, x[i].hi, a0);
+    }
+}
+
+// FP32 transform of an FP32 table (the FP32 step: the FP32 precision mode and the
+// inexact early fine steps), with the index conventions of df_transform.  The
+// inputs are the hi parts of x; the outputs are written as double-float with a
+// zero lo part.  A thread owns one output column at a time (one accumulator,
+// reset per column); with fewer than NT/2 outputs the rows are split over up to
+// 8 threads per column, whose partial sums meet in `part` (2 NT floats).
+template <bool TWO>
+__device__ void f32_transform(const float* A, int lda, int n, int nout, const df* x0, const df* x1, df* y0, df* y1,
+                              float* part)
+{
+    const int t = threadIdx.x;
+    int S = nout >= NT / 2 ? 1 : NT / nout;
+    S = S > 8 ? 8 : S;
+    if (S == 1) {
+        for (int o = t; o < nout; o += NT) {
+            const df* x = TWO ? x0 : ((o & 1) ? x1 : x0);
+            float a0 = 0.f, a1 = 0.f;
+            f32_rows<TWO>(A + o, lda, 0, n, x, a0, a1);
+            y0[o] = df{a0, 0.f};
+            if (TWO) y1[o] = df{a1, 0.f};
+        }
+        __syncthreads();
+        return;
+    }
+    const int L = ((n + S - 1) / S + 1) & ~1;   // even, so that row blocks start on even i
+    const int c = t % nout, sp = t / nout;      // S * nout <= NT
+    if (sp < S) {
+        const df* x = TWO ? x0 : ((c & 1) ? x1 : x0);
+        float a0 = 0.f, a1 = 0.f;
+        const int i0 = sp * L, i1 = i0 + L < n ? i0 + L : n;
+        if (i0 < i1) f32_rows<TWO>(A + c, lda, i0, i1, x, a0, a1);
+        part[2 * (sp * nout + c)] = a0;
+        part[2 * (sp * nout + c) + 1] = a1;
+    }
+    __syncthreads();
+    if (t < nout) {
+        float a0 = 0.f, a1 = 0.f;
+        for (int q = 0; q < S; ++q) {
+            a0 += part[2 * (q * nout + t)];
+            a1 += part[2 * (q * nout + t) + 1];
+        }
+        y0[t] = df{a0, 0.f};
+        if (TWO) y1[t] = df{a1, 0.f};
+    }
+    __syncthreads();
+}
+
+// nodes + moments + load.  fp32_only: D, f and the three transforms in FP32
+// (FP32 tables); otherwise double-float throughout.
 __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const double* tp, const double* c,
                                     double te, MixSmem& ms, double* F, bool fp32_only)
 {
@@ -178,10 +253,15 @@ __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const do
     const double* wh = tp + Tb.oWq;
     const double* aux = tp + Tb.oAux;
     const double mid2 = I.lo0 + I.hi0;
+    float* part32 = reinterpret_cast<float*>(ms.part);
     for (int k = tid; k < K; k += NT) ms.cdf[k] = df_from_double(c[k]);
     __syncthreads();
     // u at the node pairs: the odd-mode sum O (k even) into wpd, the even-mode sum E into wmd
-    df_transform<true>(Std, Qh, K, Qh, ms.cdf, nullptr, ms.wpd, ms.wmd, ms.part);
+    if (fp32_only)
+        f32_transform<true>(reinterpret_cast<const float*>(tp + Tb.oSt32), Qh, K, Qh, ms.cdf, nullptr, ms.wpd,
+                            ms.wmd, part32);
+    else
+        df_transform<true>(Std, Qh, K, Qh, ms.cdf, nullptr, ms.wpd, ms.wmd, ms.part);
     __syncthreads();
     const df* wd = reinterpret_cast<const df*>(tp + Tb.oWd);
     const df* auxd = reinterpret_cast<const df*>(tp + Tb.oAuxd);
@@ -231,11 +311,18 @@ __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const do
     __syncthreads();
     // moments g_s (even s: w (D_q + D_q'), odd s: w (D_q - D_q')) and the load (even k: f_q + f_q')
     const int ns = 2 * K + 1;
-    df_transform<false>(reinterpret_cast<const df*>(tp + Tb.oCd), ns, Qh, ns, ms.wpd, ms.wmd, ms.gdf, nullptr,
-                        ms.part);
-    __syncthreads();
-    df_transform<false>(reinterpret_cast<const df*>(tp + Tb.oSd), K, Qh, K, ms.fpd, ms.fmd, ms.ydf, nullptr,
-                        ms.part);
+    if (fp32_only) {
+        f32_transform<false>(reinterpret_cast<const float*>(tp + Tb.oC32), ns, Qh, ns, ms.wpd, ms.wmd, ms.gdf,
+                             nullptr, part32);
+        f32_transform<false>(reinterpret_cast<const float*>(tp + Tb.oS32), K, Qh, K, ms.fpd, ms.fmd, ms.ydf,
+                             nullptr, part32);
+    } else {
+        df_transform<false>(reinterpret_cast<const df*>(tp + Tb.oCd), ns, Qh, ns, ms.wpd, ms.wmd, ms.gdf, nullptr,
+                            ms.part);
+        __syncthreads();
+        df_transform<false>(reinterpret_cast<const df*>(tp + Tb.oSd), K, Qh, K, ms.fpd, ms.fmd, ms.ydf, nullptr,
+                            ms.part);
+    }
     __syncthreads();
     for (int k = tid; k < K; k += NT) F[k] = df_to_double(ms.ydf[k]);
     __syncthreads();
@@ -448,14 +535,14 @@ __device__ void residual_df(const InstDev& I, double mu, MixSmem& ms)
 }
 
 // The step: c (K, shared) -> out (K, shared).  Returns the first bad pivot or -1.
-// one_solve: stop after the first FP32 solve (no refinement; D, f and the
-// transforms stay double-float) -- the inexact fine steps of early parareal
-// iterations.
+// one_solve: run the FP32 step (FP32 transforms, D and f, one FP32 solve, no
+// refinement) -- the inexact fine steps of early parareal iterations.
 __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, const double* c,
                           const double* hist, double te, double mu, double* out, double* F, StepSmem& s,
                           MixSmem& ms, PcgSmem& cg, bool fp32_only, bool one_solve = false)
 {
     const int tid = threadIdx.x;
+    fp32_only = fp32_only || one_solve;   // the inexact step is the FP32 step
     nodes_moments_mixed(I, Tb, tp, c, te, ms, F, fp32_only);
     // refinement from x = 0: the first correction is the FP32 solve of rhs
     for (int k = tid; k < I.Kp; k += NT) {
@@ -481,7 +568,7 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
         xmax = block_max(xmax, ms.red);
         const bool small = zmax <= REFINE_TOL * xmax;
         const bool predicted = sweep >= 1 && zmax < zprev && zmax * zmax <= REFINE_EST * xmax * zprev;
-        if (fp32_only || one_solve || small || predicted || sweep >= 6 || *s.bad >= 0) break;
+        if (fp32_only || small || predicted || sweep >= 6 || *s.bad >= 0) break;
         zprev = zmax;
         if (tid == 0) ms.flag[2] += 1;
         residual_df(I, mu, ms);

@@ -50,7 +50,7 @@ __global__ void k_gauss_legendre_half(int Q, double lo, double hi, double* xh, d
 __global__ void k_basis_tables(int Mx, int Qh, double lo, double hi, const double* xh, double* St,
                                double* S, double* C, double* aux, df* Std, df* Sd, df* Cd, double* Dt,
                                df* Dtd, float* St32, float* Dt32, double* aux2, const double* wh, df* Wd,
-                               df* auxd, df* aux2d)
+                               df* auxd, df* aux2d, float* S32, float* C32)
 {
     int q = blockIdx.x;
     if (q >= Qh) return;
@@ -68,11 +68,13 @@ __global__ void k_basis_tables(int Mx, int Qh, double lo, double hi, const doubl
         Dtd[(size_t)(k - 1) * Qh + q] = df_from_double(dv);
         St32[(size_t)(k - 1) * Qh + q] = (float)v;
         Dt32[(size_t)(k - 1) * Qh + q] = (float)dv;
+        S32[(size_t)q * Mx + (k - 1)] = (float)v;
     }
     for (int s = threadIdx.x; s <= 2 * Mx; s += blockDim.x) {
         double v = cospi(s * th);
         C[(size_t)q * (2 * Mx + 1) + s] = v;
         Cd[(size_t)q * (2 * Mx + 1) + s] = df_from_double(v);
+        C32[(size_t)q * (2 * Mx + 1) + s] = (float)v;
     }
     if (threadIdx.x == 0) {
         double xa = xh[q], xb = lo + hi - xh[q];
@@ -135,7 +137,8 @@ cudaError_t launch_tables(const TableJob& job, cudaStream_t s)
                                           reinterpret_cast<df*>(job.Cd), job.Dt, reinterpret_cast<df*>(job.Dtd),
                                           reinterpret_cast<float*>(job.St32), reinterpret_cast<float*>(job.Dt32),
                                           job.aux2, job.wh, reinterpret_cast<df*>(job.Wd),
-                                          reinterpret_cast<df*>(job.auxd), reinterpret_cast<df*>(job.aux2d));
+                                          reinterpret_cast<df*>(job.auxd), reinterpret_cast<df*>(job.aux2d),
+                                          reinterpret_cast<float*>(job.S32), reinterpret_cast<float*>(job.C32));
     return cudaGetLastError();
 }
 
