@@ -1,7 +1,8 @@
 """Full-size check of the batched 1D workload in the configuration bench.py
 times: 256 instances with K in [64, 256], N = 64 m with m in [16, 64],
 alpha in {0.3, 0.5, 0.7, 1}, P = 64, mixed precision, parareal run as one
-CUDA graph with its device-driven iteration loop.
+CUDA graph with its device-driven iteration loop, with the refined F in every
+iteration and with the inexact early iterations bench.py selects.
 
 The oracle cannot solve 256 full instances in test time, so it recomputes
 sampled outputs one at a time.  Parareal's fixed point is the sequential
@@ -37,10 +38,14 @@ def _samples(wl):
     return [(big_k, P - 1), (long_m, 0), (long_m, P // 2), (be, 3 * P // 4), (other, 1), (other, P - 1)]
 
 
-def test_full_size_batched_1d_graph_parareal_against_sampled_oracle():
+@pytest.mark.parametrize("inexact", [0.0, 1e-5])
+def test_full_size_batched_1d_graph_parareal_against_sampled_oracle(inexact):
+    # inexact = 1e-5: the early iterations bench.py selects (the FP32 step on
+    # slices n > k while the increment exceeds 1e-5)
     wl = workloads.cfg2()               # the benched batch: B = 256, seed 20251011
     assert wl.B == 256 and wl.P == 64
     with psl1.Problem(wl, precision="mixed") as pr:
+        pr.set_inexact_fine(inexact)
         pr.set_graph(True)
         k = pr.solve_parareal(tol=1e-12)
         U = pr.get_coeffs("parareal")
