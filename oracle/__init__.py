@@ -22,8 +22,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "psl1_oracle.c")
 _LIB = os.path.join(_HERE, "_psl1_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "_psl1_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 D_, P_ = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
 
@@ -37,6 +39,7 @@ class Prob(ctypes.Structure):
         ("alpha", ctypes.c_double), ("T", ctypes.c_double),
         ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2),
         ("dpar", ctypes.c_double * 8), ("fpar", ctypes.c_double * 8),
+        ("solver", ctypes.c_int),
     ]
 
     @property
@@ -52,22 +55,25 @@ class Prob(ctypes.Structure):
         return self.N // self.P
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (gcc, FP64, no FMA contraction)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle shared library (gcc, FP64, no FMA contraction).
+    omp=True builds the OpenMP variant (_psl1_oracle_omp.so): the same source
+    with the parallel stage's loop over slices on all host threads."""
+    out = _LIB_OMP if omp else _LIB
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-            tmp = _LIB + f".tmp{os.getpid()}"
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+            tmp = out + f".tmp{os.getpid()}"
             subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-                                   "-o", tmp, _SRC, "-lm"])
-            os.replace(tmp, _LIB)
-    return _LIB
+                                   *(["-fopenmp"] if omp else []), "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB)
+def lib(omp: bool = False):
+    """The oracle library; omp=True: its OpenMP build (parallel stage on all host threads)."""
+    global _lib, _lib_omp
+    if (_lib_omp if omp else _lib) is None:
+        L = ctypes.CDLL(build(omp=omp))
         pp = ctypes.POINTER(Prob)
         sig = {
             "orc_b": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
@@ -82,6 +88,7 @@ def lib():
             "orc_eval_nodes": (ctypes.c_int, [pp, D_, ctypes.c_double, D_, D_, D_]),
             "orc_stiffness": (ctypes.c_int, [pp, D_, D_]),
             "orc_load": (ctypes.c_int, [pp, D_, D_]),
+            "orc_apply_stiffness": (ctypes.c_int, [pp, D_, D_, D_]),
             "orc_project": (ctypes.c_int, [pp, D_, D_]),
             "orc_chol_solve": (ctypes.c_int, [ctypes.c_int, D_, D_, D_]),
             "orc_step": (ctypes.c_int, [pp, D_, ctypes.c_double, ctypes.c_double, D_, D_]),
@@ -91,6 +98,8 @@ def lib():
             "orc_serial_uni": (ctypes.c_int, [pp, D_, D_]),
             "orc_coarse_sweep": (ctypes.c_int, [pp, D_, D_, D_, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, D_]),
+            "orc_fine_stage": (ctypes.c_int, [pp, D_, ctypes.c_int, D_]),
+            "orc_threads": (ctypes.c_int, []),
             "orc_parareal": (ctypes.c_int, [pp, D_, ctypes.c_double, ctypes.c_int, D_, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_int, D_, D_, D_, P_]),
             "orc_mlp_nparams": (ctypes.c_long, [ctypes.c_int] * 3),
@@ -106,8 +115,11 @@ def lib():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
-        _lib = L
-    return _lib
+        if omp:
+            _lib_omp = L
+        else:
+            _lib = L
+    return _lib_omp if omp else _lib
 
 
 class OracleError(RuntimeError):
@@ -130,8 +142,12 @@ def _out(*shape):
 
 
 def make_prob(*, dim=1, Mx, My=1, Qx=None, Qy=None, N, P, alpha, T=1.0, lo=(0.0, 0.0),
-              hi=(1.0, 1.0), dpar=(1.0, 0.5, 0, 0, 0, 0, 0, 0), fpar=(0.1, 0, 0, 0, 0, 0, 0, 0)) -> Prob:
-    """Problem record; Qx/Qy default to twice the modes (Gauss-Legendre)."""
+              hi=(1.0, 1.0), dpar=(1.0, 0.5, 0, 0, 0, 0, 0, 0), fpar=(0.1, 0, 0, 0, 0, 0, 0, 0),
+              solver: str = "cholesky") -> Prob:
+    """Problem record; Qx/Qy default to twice the modes (Gauss-Legendre).
+    solver: "cholesky" (dense factor of the assembled matrix) or "cg"
+    (conjugate gradients on the weak form, for mode counts whose assembly
+    is out of reach); both solve the same SPD system of each step."""
     p = Prob()
     p.dim, p.Mx = dim, Mx
     p.My = My if dim == 2 else 1
@@ -144,6 +160,7 @@ def make_prob(*, dim=1, Mx, My=1, Qx=None, Qy=None, N, P, alpha, T=1.0, lo=(0.0,
     fp = list(fpar) + [0.0] * (8 - len(fpar))
     for i in range(8):
         p.dpar[i], p.fpar[i] = dp[i], fp[i]
+    p.solver = {"cholesky": 0, "cg": 1}[solver]
     if N % P:
         raise ValueError("P must divide N")
     return p
@@ -204,6 +221,15 @@ def stiffness(p: Prob, Dq):
     A, pA = _out(p.K, p.K)
     _chk(lib().orc_stiffness(ctypes.byref(p), pD, pA), "stiffness")
     return A
+
+
+def apply_stiffness(p: Prob, Dq, v):
+    """(A v)_i by the weak form, node by node, without forming A."""
+    Dq, pD = _d(Dq)
+    v, pv = _d(v)
+    out, po = _out(p.K)
+    _chk(lib().orc_apply_stiffness(ctypes.byref(p), pD, pv, po), "apply_stiffness")
+    return out
 
 
 def load(p: Prob, fq):
@@ -288,8 +314,9 @@ def coarse_sweep(p: Prob, u0, mlp=None):
     return U
 
 
-def parareal(p: Prob, u0, tol: float, max_iter: int | None = None, mlp=None):
-    """Returns (U[k, n, :] for k = 0..iters, errlog[:iters], iters)."""
+def parareal(p: Prob, u0, tol: float, max_iter: int | None = None, mlp=None, omp: bool = False):
+    """Returns (U[k, n, :] for k = 0..iters, errlog[:iters], iters).
+    omp=True runs the parallel stage of each iteration on all host threads."""
     if max_iter is None:
         max_iter = p.P
     u0, pu = _d(u0)
@@ -297,10 +324,23 @@ def parareal(p: Prob, u0, tol: float, max_iter: int | None = None, mlp=None):
     err, pe = _out(max(max_iter, 1))
     it = ctypes.c_int(0)
     keep = _mlp_args(mlp)
-    _chk(lib().orc_parareal(ctypes.byref(p), pu, float(tol), int(max_iter), keep[1], keep[2], keep[3],
-                            keep[4], keep[5], keep[7], pU, pe, ctypes.byref(it)), "parareal")
+    _chk(lib(omp).orc_parareal(ctypes.byref(p), pu, float(tol), int(max_iter), keep[1], keep[2], keep[3],
+                               keep[4], keep[5], keep[7], pU, pe, ctypes.byref(it)), "parareal")
     k = it.value
     return Uall[: k + 1], err[:k], k
+
+
+def fine_stage(p: Prob, U, n0: int = 0, omp: bool = False):
+    """F_n(U_{0:n}) for n = n0..P-1 (rows n0.. of a P x K array; rows < n0 zero)."""
+    U, pU = _d(U)
+    F, pF = _out(p.P, p.K)
+    _chk(lib(omp).orc_fine_stage(ctypes.byref(p), pU, int(n0), pF), "fine_stage")
+    return F
+
+
+def threads(omp: bool = False) -> int:
+    """Host threads of the (OpenMP) parallel stage."""
+    return int(lib(omp).orc_threads())
 
 
 def mlp_nparams(nin, width, nout) -> int:

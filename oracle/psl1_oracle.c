@@ -33,6 +33,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -58,6 +61,8 @@ typedef struct {
     double lo[2], hi[2];/* box Omega = (lo0,hi0) x (lo1,hi1) */
     double dpar[8];
     double fpar[8];
+    int solver;         /* step solve: 0 dense Cholesky of the assembled matrix,
+                           1 conjugate gradients on the weak form (no matrix) */
 } orc_prob;
 
 /* ------------------------------------------------------------------------ */
@@ -323,11 +328,116 @@ int orc_chol_solve(int K, const double* M, const double* rhs, double* x)
     return 0;
 }
 
+/* The stiffness operator without a matrix: the weak form (Eq. AForm)
+ *   (A v)_i = a(v, phi_i) = sum_q w_q D_q grad v(x_q) . grad phi_i(x_q),
+ *   grad v(x_q) = sum_j v_j grad phi_j(x_q),
+ * the same quadrature sum as the assembled A_ij v_j, taken node by node.    */
+static void apply_stiffness(const orc_prob* p, const orc_disc* d, const double* Dq, const double* v,
+                            double* out)
+{
+    int K = d->K;
+    for (int i = 0; i < K; ++i) out[i] = 0.0;
+    for (int q = 0; q < d->Q; ++q) {
+        const double* gx = d->gx + (size_t)q * K;
+        const double* gy = d->gy + (size_t)q * K;
+        double vx = 0.0, vy = 0.0;
+        for (int j = 0; j < K; ++j) vx += gx[j] * v[j];
+        if (p->dim == 2)
+            for (int j = 0; j < K; ++j) vy += gy[j] * v[j];
+        double s = d->wq[q] * Dq[q];
+        for (int i = 0; i < K; ++i) {
+            double g = gx[i] * vx;
+            if (p->dim == 2) g += gy[i] * vy;
+            out[i] += s * g;
+        }
+    }
+}
+
+/* The same SPD system (I + mu A) c_new = rhs solved by conjugate gradients
+ * with the Jacobi preconditioner (diagonal 1 + mu sum_q w_q D_q |grad
+ * phi_i|^2), the operator applied by apply_stiffness.  The system is
+ * symmetric positive definite for D > 0 (Sec. 2.1), so CG converges; the
+ * iteration stops once the residual is at rounding level,
+ * ||rhs - M c|| <= 1e-15 ||rhs||, or stagnates (4 K iterations at most).
+ * Returns 0, -1 on allocation failure, or -2 if p . M p <= 0 (not SPD).    */
+static int solve_cg(const orc_prob* p, const orc_disc* d, const double* Dq, double mu, const double* rhs,
+                    double* x)
+{
+    int K = d->K;
+    double *dg = malloc(sizeof(double) * K), *r = malloc(sizeof(double) * K), *z = malloc(sizeof(double) * K);
+    double *pp = malloc(sizeof(double) * K), *Ap = malloc(sizeof(double) * K);
+    if (!dg || !r || !z || !pp || !Ap) { free(dg); free(r); free(z); free(pp); free(Ap); return -1; }
+    for (int i = 0; i < K; ++i) dg[i] = 0.0;
+    for (int q = 0; q < d->Q; ++q)
+        for (int i = 0; i < K; ++i) {
+            double g = d->gx[(size_t)q * K + i] * d->gx[(size_t)q * K + i];
+            if (p->dim == 2) g += d->gy[(size_t)q * K + i] * d->gy[(size_t)q * K + i];
+            dg[i] += d->wq[q] * Dq[q] * g;
+        }
+    double bb = 0.0, rz = 0.0;
+    for (int i = 0; i < K; ++i) {
+        dg[i] = 1.0 + mu * dg[i];
+        x[i] = 0.0;
+        r[i] = rhs[i];
+        z[i] = r[i] / dg[i];
+        pp[i] = z[i];
+        bb += rhs[i] * rhs[i];
+        rz += r[i] * z[i];
+    }
+    int st = 0;
+    for (int it = 0; it < 4 * K + 10 && bb > 0.0; ++it) {
+        apply_stiffness(p, d, Dq, pp, Ap);
+        double pAp = 0.0;
+        for (int i = 0; i < K; ++i) {
+            Ap[i] = pp[i] + mu * Ap[i];
+            pAp += pp[i] * Ap[i];
+        }
+        if (!(pAp > 0.0)) { st = -2; break; }
+        double a = rz / pAp, rr = 0.0, rzn = 0.0;
+        for (int i = 0; i < K; ++i) {
+            x[i] += a * pp[i];
+            r[i] -= a * Ap[i];
+            z[i] = r[i] / dg[i];
+            rr += r[i] * r[i];
+            rzn += r[i] * z[i];
+        }
+        if (rr <= 1e-30 * bb) break;
+        double beta = rzn / rz;
+        rz = rzn;
+        for (int i = 0; i < K; ++i) pp[i] = z[i] + beta * pp[i];
+    }
+    free(dg); free(r); free(z); free(pp); free(Ap);
+    return st;
+}
+
 /* One linearised step: (I + mu A(D(t_e, c_prev))) c_new = hist + mu F(f(t_e, c_prev)).
- * hist is every history term of the right-hand side (already summed).      */
+ * hist is every history term of the right-hand side (already summed).
+ * p->solver selects the solve of the (unique) solution: the dense Cholesky
+ * factor of the assembled matrix, or conjugate gradients on the weak form
+ * (for mode counts whose K x K x Q assembly is out of reach).             */
+static int step_solve_cg(const orc_prob* p, const orc_disc* d, const double* cprev, double te,
+                         double mu, const double* hist, double* cnew)
+{
+    int K = d->K, Q = d->Q, st;
+    double* uq = malloc(sizeof(double) * Q);
+    double* Dq = malloc(sizeof(double) * Q);
+    double* fq = malloc(sizeof(double) * Q);
+    double* F = malloc(sizeof(double) * K);
+    double* r = malloc(sizeof(double) * K);
+    if (!uq || !Dq || !fq || !F || !r) { st = -1000000; goto out; }
+    eval_nodes(p, d, cprev, te, uq, Dq, fq);
+    load(d, fq, F);
+    for (int i = 0; i < K; ++i) r[i] = hist[i] + mu * F[i];
+    st = solve_cg(p, d, Dq, mu, r, cnew);
+out:
+    free(uq); free(Dq); free(fq); free(F); free(r);
+    return st;
+}
+
 static int step_solve(const orc_prob* p, const orc_disc* d, const double* cprev, double te,
                       double mu, const double* hist, double* cnew)
 {
+    if (p->solver == 1) return step_solve_cg(p, d, cprev, te, mu, hist, cnew);
     int K = d->K, Q = d->Q, st;
     double* uq = malloc(sizeof(double) * Q);
     double* Dq = malloc(sizeof(double) * Q);
@@ -386,6 +496,15 @@ int orc_stiffness(const orc_prob* p, const double* Dq, double* A)
     orc_disc d;
     if (disc_build(p, &d)) return -1;
     stiffness(p, &d, Dq, A);
+    disc_free(&d);
+    return 0;
+}
+
+int orc_apply_stiffness(const orc_prob* p, const double* Dq, const double* v, double* out)
+{
+    orc_disc d;
+    if (disc_build(p, &d)) return -1;
+    apply_stiffness(p, &d, Dq, v, out);
     disc_free(&d);
     return 0;
 }
@@ -812,6 +931,52 @@ int orc_coarse_sweep(const orc_prob* p, const double* u0, double* U, const doubl
 }
 
 /* ------------------------------------------------------------------------ */
+/* Parallel stage of a parareal iteration: for every slice n >= n0,          */
+/* G_old(n) = G_n(U_{0:n}) (when Gold is not NULL) and F_old(n) = F_n(U_{0:n}).*/
+/* The slices are independent, so the loop over n runs on all host threads  */
+/* when this file is compiled with OpenMP, as the paper runs its parallel    */
+/* stage with one thread per coarse interval (Sec. 4.2); without OpenMP the  */
+/* pragma is ignored.  Each slice is computed the same way either way.       */
+/* ------------------------------------------------------------------------ */
+static int parallel_stage(const orc_prob* p, const orc_disc* d, const double* U, const orc_mlp* mp, int n0,
+                          double* Gold, double* Fold)
+{
+    int K = d->K, P = p->P, m = p->N / p->P, st = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(min : st)
+    for (int n = n0; n < P; ++n) {
+        double* V = malloc(sizeof(double) * (size_t)(m + 1) * K);
+        int sn = V ? 0 : -1000000;
+        if (sn == 0 && Gold) sn = coarse_step(p, d, n, U, mp, Gold + (size_t)n * K);
+        if (sn == 0) sn = fine_slice(p, d, n, U, V);
+        if (sn == 0) memcpy(Fold + (size_t)n * K, V + (size_t)m * K, sizeof(double) * K);
+        free(V);
+        if (sn < st) st = sn;
+    }
+    return st;
+}
+
+/* F_n(U_{0:n}) of the slices n = n0..P-1 into Fold (row n), for timing the
+ * parallel stage alone.                                                      */
+int orc_fine_stage(const orc_prob* p, const double* U, int n0, double* Fold)
+{
+    orc_disc d;
+    if (disc_build(p, &d)) return -1;
+    int st = parallel_stage(p, &d, U, NULL, n0, NULL, Fold);
+    disc_free(&d);
+    return st;
+}
+
+/* Host threads the parallel stage runs on (1 without OpenMP).               */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
 /* Parareal (Sec. 2.2 steps 1-2, Eq. Parareal, flowchart Fig. parareal):     */
 /*   U^0_0 = u0, U^0_{n+1} = G_n(U^0_{0:n});                                 */
 /*   iteration k: parallel stage G_old(n) = G_n(U^k_{0:n}),                  */
@@ -850,12 +1015,8 @@ int orc_parareal(const orc_prob* p, const double* u0, double tol, int max_iter,
     while (st == 0 && k < max_iter) {
         const double* Uk = Uall + (size_t)k * slab;
         double* Uk1 = Uall + (size_t)(k + 1) * slab;
-        /* parallel stage */
-        for (int n = 0; n < P && st == 0; ++n) {
-            st = coarse_step(p, &d, n, Uk, mp, Gold + (size_t)n * K);
-            if (st == 0) st = fine_slice(p, &d, n, Uk, V);
-            memcpy(Fold + (size_t)n * K, V + (size_t)m * K, sizeof(double) * K);
-        }
+        /* parallel stage (the slices are independent given U^k) */
+        st = parallel_stage(p, &d, Uk, mp, 0, Gold, Fold);
         if (st) break;
         /* sequential coarse sweep with correction */
         memcpy(Uk1, u0, sizeof(double) * K);

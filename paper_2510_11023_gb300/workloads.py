@@ -62,6 +62,8 @@ class Workload:
 D_CFG1 = (1.0, 0.5, 0, 0, 0, 0, 0, 0)          # 1 + 0.5/(1+u^2)
 D_CFG2 = (1.0, 0.5, 0, 0, 0.2, 0, 0, 0)        # (1 + 0.5/(1+u^2)) (1 + 0.2 sin 2 pi x)
 F_COS = (0.1, 0, 0, 0, 0, 0, 0, 0)             # 0.1 cos u
+D_CFG5 = (1.0, 0.5, 0, 0, 0, 0, 0, 0.3)        # 1 + 0.5/(1+u^2) (1 + 0.3 cos 2 pi y)
+F_SIN = (0, 0.1, 0, 0, 0, 0, 0, 0)             # 0.1 sin u
 
 
 def cfg1(K: int = 32, N: int = 256, P: int = 8, alpha: float = 0.5) -> Workload:
@@ -153,8 +155,7 @@ def cfg5(B: int = 16, M: int = 64, N: int = 8192, P: int = 256, alpha: float = 0
     rng = np.random.default_rng(seed)
     specs, u0 = [], []
     for _ in range(B):
-        specs.append(InstanceSpec(dim=2, modes=(M, M), nsteps=N, alpha=alpha, dpar=(1.0, 0.5, 0, 0, 0, 0, 0, 0.3),
-                                  fpar=(0, 0.1, 0, 0, 0, 0, 0, 0)))
+        specs.append(InstanceSpec(dim=2, modes=(M, M), nsteps=N, alpha=alpha, dpar=D_CFG5, fpar=F_SIN))
         u0.append(_u0_2d(rng, M, M))
     return Workload("2D batched B=%d M=%d x %d N=%d P=%d alpha=%g" % (B, M, M, N, P, alpha), P, specs, u0,
                     {"seed": seed})

@@ -1,8 +1,9 @@
 """GPU parity of the 2D tensor-product path against the CPU oracle, through the
 C ABI: single steps (FP64 and mixed paths) over ragged shapes, boxes and
 coefficient families, the fine and coarse propagators, the serial solvers and
-parareal on a small ragged 2D batch, one full-size 32 x 32-mode step, and the
-diagonal-solve property at 64 x 64 modes.
+parareal on a small ragged 2D batch, full-size steps at 32 x 32 and 64 x 64
+modes and a 64 x 64-mode fine propagator against stored oracle results, and
+the diagonal-solve property at 64 x 64 modes.
 
 Tolerances: FP64 path 1e-10 relative (the solve is CG to a relative residual of
 1e-14); mixed path the same on solves (refinement residual in double-float,
@@ -140,6 +141,34 @@ def test_full_size_step_32x32_modes(prec):
     with psl1.Problem([spec], P, precision=prec) as pr:
         g = pr.step(0, c, te, mu, hist)
     assert rel(g, ref) < 1e-11, rel(g, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_step_64x64_modes_varying_D(prec):
+    # one L1 step at the 64 x 64-mode, 128 x 128-node size of the 2D batched workload,
+    # with its y-dependent D and f = 0.1 sin u (node arrays in the slot's global
+    # workspace), against the oracle's stored result (tests/golden/make_2d_64x64.py)
+    sys.path.insert(0, GOLDEN)
+    from make_2d_64x64 import step_inputs
+    spec, P, c, hist, te, mu = step_inputs()
+    ref = np.loadtxt(os.path.join(GOLDEN, "step2d_64x64.txt"))
+    with psl1.Problem([spec], P, precision=prec) as pr:
+        g = pr.step(0, c, te, mu, hist)
+    assert rel(g, ref) < 1e-11, rel(g, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_fine_propagator_64x64_modes(prec):
+    # F_2 with two fine steps at 64 x 64 modes: fine history in the ring, the coarse
+    # history of U_0..U_2 (Eq. L1Fine) and the global-workspace node arrays, against
+    # the oracle's stored final state (tests/golden/make_2d_64x64.py)
+    sys.path.insert(0, GOLDEN)
+    from make_2d_64x64 import fine_inputs
+    spec, P, n, U = fine_inputs()
+    ref = np.loadtxt(os.path.join(GOLDEN, "fine2d_64x64.txt"))
+    with psl1.Problem([spec], P, precision=prec) as pr:
+        V = pr.fine_slice(0, n, U)
+    assert rel(V[-1], ref) < 1e-11, rel(V[-1], ref)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

@@ -290,6 +290,84 @@ def test_cholesky_reports_first_bad_pivot():
 
 
 # ---------------------------------------------------------------- schemes
+def test_weak_form_operator_closed_form_and_matrix():
+    # the matrix-free weak form (Eq. AForm, node by node) gives
+    # (i) pi^2 (k^2 + l^2) v_kl for D = 1 on the unit square (closed form) and
+    # (ii) the assembled matrix times v (numpy) for a random positive D, 1D and 2D
+    p = O.make_prob(dim=2, Mx=5, My=4, Qx=32, Qy=32, N=4, P=1, alpha=0.5)
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(p.K)
+    k = np.repeat(np.arange(1, 6), 4)
+    l = np.tile(np.arange(1, 5), 5)
+    ref = math.pi**2 * (k**2 + l**2) * v
+    assert np.abs(O.apply_stiffness(p, np.ones(p.Q), v) - ref).max() < 1e-11 * np.abs(ref).max()
+    for q in (O.make_prob(Mx=17, N=4, P=1, alpha=0.5),
+              O.make_prob(dim=2, Mx=6, My=7, Qx=14, Qy=12, N=4, P=1, alpha=0.5, lo=(-0.5, 0.25), hi=(1.0, 2.0))):
+        Dq = 0.5 + rng.random(q.Q)
+        v = rng.standard_normal(q.K)
+        ref = O.stiffness(q, Dq) @ v
+        assert np.abs(O.apply_stiffness(q, Dq, v) - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_cg_step_solves_the_same_system_as_cholesky():
+    # the two step solves of the oracle reach the same (unique) solution of the SPD
+    # system of Eq. NumericalSchemeFine; with D = d0 and f = 0 it is the diagonal solve
+    Mx, My, d0, mu = 6, 5, 1.3, 0.07
+    lo, hi = (-0.5, 0.25), (1.0, 2.0)
+    p = O.make_prob(dim=2, Mx=Mx, My=My, Qx=48, Qy=48, N=4, P=1, alpha=0.5, lo=lo, hi=hi,
+                    dpar=(d0, 0, 0, 0), fpar=(0,), solver="cg")
+    Lx, Ly = hi[0] - lo[0], hi[1] - lo[1]
+    rng = np.random.default_rng(3)
+    hist = rng.standard_normal(Mx * My)
+    k = np.repeat(np.arange(1, Mx + 1), My)
+    l = np.tile(np.arange(1, My + 1), Mx)
+    ref = hist / (1 + mu * d0 * math.pi**2 * (k**2 / Lx**2 + l**2 / Ly**2))
+    assert np.abs(O.step(p, rng.standard_normal(Mx * My), 0.3, mu, hist) - ref).max() < 1e-13
+    for dim, Mx, My in ((1, 40, 1), (2, 9, 8)):
+        kw = dict(dim=dim, Mx=Mx, My=My, N=12, P=3, alpha=0.6, dpar=(1.0, 0.5, 0, 0, 0.2, 0, 0, 0.3),
+                  fpar=(0.05, 0.1, 0.02, 0, 0, 0))
+        pc, pg = O.make_prob(**kw), O.make_prob(solver="cg", **kw)
+        c = rng.standard_normal(pc.K) / np.arange(1, pc.K + 1)
+        hist = c + 0.01 * rng.standard_normal(pc.K)
+        for mu in (0.01, 0.8):
+            a, b = O.step(pc, c, 0.2, mu, hist), O.step(pg, c, 0.2, mu, hist)
+            assert np.abs(a - b).max() < 1e-13 * np.abs(a).max(), (dim, mu)
+        U = O.coarse_sweep(pc, c)
+        Va, Vb = O.fine_slice(pc, 2, U[:3]), O.fine_slice(pg, 2, U[:3])
+        assert np.abs(Va - Vb).max() < 1e-13 * np.abs(Va).max(), dim
+
+
+def test_cg_step_reproduces_the_stored_dense_solve_at_32x32_modes():
+    # at the 32 x 32-mode, 64 x 64-node size the CG solve on the weak form reproduces
+    # the dense Cholesky solve stored in tests/golden/step2d_32x32.txt (written from the
+    # assembled K x K x Q matrix), so the 64 x 64-mode stored results, which only the
+    # CG solve can reach, rest on the same system
+    import os
+    import sys
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, golden)
+    from make_step2d_32x32 import inputs
+    spec, P, c, hist, te, mu = inputs()
+    p = O.make_prob(dim=2, Mx=32, My=32, N=spec.nsteps, P=P, alpha=spec.alpha, dpar=spec.dpar, fpar=spec.fpar,
+                    solver="cg")
+    ref = np.loadtxt(os.path.join(golden, "step2d_32x32.txt"))
+    assert np.abs(O.step(p, c, te, mu, hist) - ref).max() < 1e-14 * np.abs(ref).max()
+
+
+def test_openmp_parallel_stage_is_the_same_computation():
+    # the OpenMP build runs the parallel stage's slices on all host threads (the
+    # paper's threads over coarse intervals, Sec. 4.2); every slice is computed the
+    # same way, so parareal and the F stage agree bitwise with the serial build
+    p = O.make_prob(Mx=12, N=48, P=6, alpha=0.35, dpar=(1, 0.5, 0, 0, 0.2), fpar=CFG1_F)
+    u0 = cfg1_u0(12)
+    U1, e1, k1 = O.parareal(p, u0, 1e-12)
+    U2, e2, k2 = O.parareal(p, u0, 1e-12, omp=True)
+    assert k1 == k2 and np.array_equal(U1, U2) and np.array_equal(e1, e2)
+    assert np.array_equal(O.fine_stage(p, U1[0], 2), O.fine_stage(p, U1[0], 2, omp=True))
+    F = O.fine_stage(p, U1[0], 2)
+    assert np.array_equal(F[3], O.fine_slice(p, 3, U1[0][:4])[-1]) and not F[:2].any()
+
+
 def test_fine_propagator_expanded_equals_difference_form():
     # Eq. (L1Fine): difference form (first line) = expanded form (second line)
     p = O.make_prob(Mx=12, N=48, P=6, alpha=0.35, dpar=(1, 0.5, 0, 0, 0.2), fpar=CFG1_F)
