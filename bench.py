@@ -7,10 +7,13 @@ sweeps with correction, stopping test) of the batched 1D workload: 256
 instances with seeded uneven K in [64,256], N = 64 m with m in [16,64]
 (N in [1024,4096]), alpha in {0.3,0.5,0.7,1.0}, P = 64 slices.  The error is
 measured against the sequential fine sweep S_hyb (parareal's fixed point)
-solved on the GPU in plain FP64; the stopping tolerance on the increment is
-picked during warm-up as the loosest one that still reaches 1e-8.
+solved on the GPU in plain FP64.  The stopping rule is fixed in advance: the
+increment tolerance is one tenth of the target error (1e-9); the loosest
+tolerance that still reaches 1e-8 (found with the reference solution, which
+a user does not have) is reported beside it as context only.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --workload uniform-history    (the uniform solver's history stream case)
 Under torchrun each rank solves its own batch (seed + rank): weak scaling,
 no collective on the data path; rank 0 prints one JSON line.
 """
@@ -33,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "parareal wall-time to rel err 1e-8 vs serial GPU solve; fine steps*modes/s"
 UNIT = "fine_steps*modes/s"
 TARGET = 1e-8
+FIXED_TOL = TARGET / 10        # increment tolerance of the stopping rule, fixed in advance
 INEXACT_ABOVE = (1e-4, 1e-5)   # increments above which early F stages take the FP32 step (candidates)
 
 
@@ -43,9 +47,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "fp32"])
-    ap.add_argument("--workload", default="batched1d", choices=["batched1d", "2d", "2d-batched"],
+    ap.add_argument("--workload", default="batched1d", choices=["batched1d", "2d", "2d-batched", "uniform-history"],
                     help="batched1d: the headline 1D batch; 2d: one 32 x 32-mode instance, N = 2048, P = 128; "
-                         "2d-batched: --batch instances of 64 x 64 modes, N = 8192, P = 256")
+                         "2d-batched: --batch instances of 64 x 64 modes, N = 8192, P = 256; uniform-history: "
+                         "the uniform serial solve of 96 instances, K = 256, N = 1024 (history stream from HBM)")
     ap.add_argument("--batch", type=int, default=0, help="instances (0: 256 for batched1d, 16 for 2d-batched)")
     ap.add_argument("--seed", type=int, default=20251011)
     ap.add_argument("--no-e2e", action="store_true")
@@ -55,6 +60,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=0.0,
                     help="CPU seconds per reference-arm step (0: about 2 minutes in total)")
+    ap.add_argument("--no-ref-context", action="store_true",
+                    help="reference arm: skip the oracle's whole solves of the small configurations")
     ap.add_argument("--coarse", default="auto", choices=["auto", "l1", "learned"],
                     help="coarse propagator; auto: the faster to rel err 1e-8 in warm-up")
     ap.add_argument("--inexact", default="auto", choices=["auto", "on", "off"],
@@ -201,53 +208,157 @@ def oracle_throughput_2d(wl, seconds: float) -> tuple:
     return nstep * s.K / (dt * scale), dt, nstep
 
 
-def oracle_throughput(wl, S, seconds: float) -> tuple:
-    """The FP64 oracle (single thread) on a bounded sample of the workload:
-    fine propagators of the middle slice of successive instances (history from
-    S, or from the oracle's coarse sweep), until `seconds` of CPU time are spent."""
+_HIST_CACHE: dict = {}
+
+
+def oracle_throughput(wl, S, seconds: float, omp: bool = True) -> tuple:
+    """The FP64 oracle on a bounded sample of the workload: for successive
+    instances, the fine propagators F_n of the slices n = P/2 .. P/2 + T - 1
+    (T = host threads of the OpenMP build, one slice per thread, as the paper
+    runs its parallel stage; T = 1 for the serial build), until `seconds` of
+    timed CPU work are spent.  Their history U_{0:n} comes from S (the GPU
+    serial solve) or from the oracle's coarse sweep, computed outside the timed
+    region.  Returns (fine step-modes per second, timed seconds, instances, T)."""
     import oracle as O
     if wl.specs[0].dim == 2:
-        return oracle_throughput_2d(wl, seconds)
-    O.build()
-    n = wl.P // 2
-    work, t0, inst = 0.0, time.perf_counter(), 0
-    while time.perf_counter() - t0 < seconds and inst < wl.B:
+        v, dt, n = oracle_throughput_2d(wl, seconds)
+        return v, dt, n, 1
+    O.build(omp=omp)
+    T = O.threads(omp)
+    n0 = wl.P // 2
+    n1 = min(wl.P, n0 + T)
+    work, timed, inst = 0.0, 0.0, 0
+    while timed < seconds and inst < wl.B:
         s = wl.specs[inst]
         op = oracle_prob(s, wl.P)
-        U = S[inst][: n + 1] if S is not None else O.coarse_sweep(op, wl.u0[inst])[: n + 1]
-        O.fine_slice(op, n, U, diff_form=True)
-        work += (s.nsteps // wl.P) * s.K
+        if S is not None:
+            U = S[inst][:n1]
+        else:
+            key = (id(wl), inst)
+            if key not in _HIST_CACHE:
+                _HIST_CACHE[key] = O.coarse_sweep(op, wl.u0[inst])[:n1]
+            U = _HIST_CACHE[key]
+        t0 = time.perf_counter()
+        O.fine_stage(op, U, n0, n1, omp=omp)
+        timed += time.perf_counter() - t0
+        work += (n1 - n0) * (s.nsteps // wl.P) * s.K
         inst += 1
-    dt = time.perf_counter() - t0
-    return work / dt, dt, inst
+    return work / timed, timed, inst, T
+
+
+def oracle_paper_shapes() -> dict:
+    """Whole solves by the oracle on the small configurations: the plain 1D
+    case (K = 32, N = 256, P = 8) and the paper's model-problem shape
+    (K = 16, P = 256, m = 32): S_uni, S_hyb and parareal (tolerance 1e-10, the
+    paper's) on one thread, and parareal with its parallel stage on all host
+    threads (OpenMP build).  Seconds per solve."""
+    import oracle as O
+    from paper_2510_11023_gb300 import workloads
+    out = {}
+    for name, wl in (("1d_plain_K32_N256_P8", workloads.cfg1()), ("paper_shape_K16_P256_m32", workloads.e1())):
+        s = wl.specs[0]
+        op = oracle_prob(s, wl.P)
+        u0 = wl.u0[0]
+        r = {"fine_steps_x_modes": s.nsteps * s.K}
+        for key, fn in (("serial_uniform_s", lambda: O.serial_uni(op, u0)),
+                        ("serial_hybrid_s", lambda: O.serial_hyb(op, u0))):
+            t0 = time.perf_counter()
+            fn()
+            r[key] = time.perf_counter() - t0
+        for omp in (False, True):
+            t0 = time.perf_counter()
+            _, _, k = O.parareal(op, u0, 1e-10, omp=omp)
+            r["parareal_s_threads%d" % O.threads(omp)] = time.perf_counter() - t0
+            r["parareal_iterations"] = k
+        out[name] = r
+    return out
 
 
 def reference_arm(args, dist: Dist):
-    from paper_2510_11023_gb300 import workloads
     if dist.rank != 0:
         return
     wl = make_workload(args)
     per_step = args.ref_step_seconds or max(2.0, 120.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         oracle_throughput(wl, None, per_step / 4)
-    vals, secs = [], []
+    vals, secs, cores = [], [], 1
     for _ in range(args.steps):
-        v, dt, ninst = oracle_throughput(wl, None, per_step)
+        v, dt, ninst, cores = oracle_throughput(wl, None, per_step)
         vals.append(v)
         secs.append(dt)
     v = float(np.mean(vals))
-    sample = (f"oracle fine propagator F_n (n = P/2, coarse-sweep history) of successive instances of the "
-              f"batched workload, ~{per_step:.0f} s per step, 1 thread")
+    sample = (f"oracle fine propagators F_n, n = P/2 .. P/2+{cores - 1}, one per host thread (OpenMP build), "
+              f"of successive instances of the batched workload, ~{per_step:.0f} s of timed work per step; "
+              f"their coarse-sweep history computed outside the timed region")
     if wl.specs[0].dim == 2:
         sample = (f"oracle L1 steps of the instance with half the modes per axis, ~{per_step:.0f} s per step, "
                   f"scaled by the oracle's K^2 Q cost to the full size, 1 thread")
+    extra = {}
+    if wl.specs[0].dim == 1 and not args.no_ref_context:
+        extra["oracle_paper_shapes"] = oracle_paper_shapes()
+        # the serial solve S_hyb of a 16-instance subset of the batched workload, extrapolated
+        # from the single-thread sample rate (an oracle step costs the same inside S_hyb)
+        v1, dt1, n1, _ = oracle_throughput(wl, None, 10.0, omp=False)
+        sub = wl.specs[:16]
+        extra["oracle_batched_subset16"] = {
+            "fine_steps_x_modes": float(sum(s_.nsteps * s_.K for s_ in sub)),
+            "rate_1thread": v1, "rate_all_threads": v, "threads": cores,
+            "serial_hybrid_s_extrapolated": float(sum(s_.nsteps * s_.K for s_ in sub)) / v1,
+            "how": "rates of the fine-propagator sample above; S_hyb time = the subset's fine steps x modes / rate"}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl.name, "batch": wl.B, "P": wl.P},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "host_cpus": os.cpu_count()},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}, **extra}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- algorithmic work
+def alg_flops_step_1d(K: int, Q: int) -> float:
+    """Algorithmic FLOPs of one linearised 1D step with the assembly in use:
+    values at the Q nodes and the load vector (4 Q K), the 2K+1 quadrature
+    moments of the Toeplitz+Hankel stiffness (2 Q (2K+1)), and the SPD solve
+    counted as a direct solve (Cholesky K^3/3 and two triangular solves 2 K^2)."""
+    return 4.0 * Q * K + 2.0 * Q * (2 * K + 1) + K**3 / 3.0 + 2.0 * K * K
+
+
+def fstage_alg_flops(wl, iters) -> tuple:
+    """(algorithmic FLOPs of all F-stage launches of a solve, launches): at
+    iteration k every instance still iterating runs its slices n = k..P-1."""
+    total = 0.0
+    for s, it in zip(wl.specs, iters):
+        m = s.nsteps // wl.P
+        steps = sum((wl.P - k) * m for k in range(int(it)))
+        total += steps * alg_flops_step_1d(s.K, s.Q)
+    return total, int(max(iters))
+
+
+def uniform_history_case(args):
+    """The uniform serial solve S_uni of 96 instances with K = 256 modes and
+    N = 1024 fine steps (mixed precision): 2 MB of fine history per instance,
+    192 MB in all, more than L2, so every history launch (k_uni_hist) streams
+    from HBM.  The first solve tunes the stream and captures its graph; the
+    second is timed."""
+    import torch
+    from paper_2510_11023_gb300 import psl1, workloads
+    specs = [workloads.InstanceSpec(modes=(256, 1), nsteps=1024, alpha=0.5, dpar=workloads.D_CFG2,
+                                    fpar=workloads.F_COS) for _ in range(96)]
+    rng = np.random.default_rng(1)
+    u0 = [rng.standard_normal(256) * np.arange(1, 257) ** -2.0 for _ in specs]
+    wl = workloads.Workload("uniform history case: 96 x (K=256, N=1024)", 64, specs, u0)
+    stream = torch.cuda.current_stream()
+    with psl1.Problem(wl, precision="mixed", stream=stream.cuda_stream) as pr:
+        pr.solve_serial("uniform")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pr.solve_serial("uniform")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    hist_bytes = sum(s.K * 8 * s.nsteps * (s.nsteps - 1) / 2 for s in specs)
+    print(json.dumps({"workload": wl.name, "uniform_solve_ms": ms, "history_bytes": hist_bytes}), flush=True)
 
 
 # ---------------------------------------------------------------- our arm
@@ -261,6 +372,10 @@ def main():
     import torch
     from paper_2510_11023_gb300 import psl1, workloads
 
+    if args.workload == "uniform-history":
+        psl1.load()
+        uniform_history_case(args)
+        return
     dist = Dist(args.gpus, "nccl")
     torch.cuda.set_device(dist.local)
     stream = torch.cuda.current_stream()
@@ -268,7 +383,8 @@ def main():
     fp64_tf, fp32_tf = psl1.psl1_probe_peaks()
 
     wl = make_workload(args, dist.rank)
-    if wl.specs[0].dim == 2:
+    dim2 = wl.specs[0].dim == 2
+    if dim2:
         args.coarse = "l1"          # the learned correction is defined for 1D instances
     u0 = wl.u0_concat()
     d_u0 = torch.from_numpy(u0).to("cuda")
@@ -312,19 +428,12 @@ def main():
                       "epochs": args.train_epochs, "loss_first": float(log[0]), "loss_last": float(log[-1]),
                       "seed": args.seed + 7919}
 
-    def tune(coarse, inexact=0.0):
-        """Loosest increment tolerance that reaches the target error; its solve time."""
+    def configure(coarse, inexact):
         pr.set_coarse(mlp if coarse == "learned" else None)
         pr.set_inexact_fine(inexact)
+
+    def timed_solve(tol_):
         pr.set_u0_dev(d_u0.data_ptr())
-        tol_ = 1.6e-7          # halved until the iterate meets the target error
-        while True:
-            pr.solve_parareal(tol=tol_, allow_not_converged=True)
-            if rel_err(pr.get_coeffs("parareal"), S) <= TARGET or tol_ < 1e-13:
-                break
-            tol_ /= 2.0
-        for _ in range(max(args.warmup - 1, 0)):
-            pr.solve_parareal(tol=tol_, allow_not_converged=True)
         e0.record(stream)
         pr.solve_parareal(tol=tol_, allow_not_converged=True)
         e1.record(stream)
@@ -332,23 +441,41 @@ def main():
         return {"tol": tol_, "ms": e0.elapsed_time(e1), "iterations": int(pr.get_iterations().max()),
                 "rel_err": rel_err(pr.get_coeffs("parareal"), S)}
 
-    cands = {}
-    for c in (["l1", "learned"] if args.coarse == "auto" else [args.coarse]):
-        cands[c] = tune(c)
-    coarse = min(cands, key=lambda c: cands[c]["ms"])
+    def trial(coarse, inexact=0.0):
+        """The solve at the fixed stopping rule with this configuration (after warm-up)."""
+        configure(coarse, inexact)
+        for _ in range(max(args.warmup - 1, 0)):
+            pr.set_u0_dev(d_u0.data_ptr())
+            pr.solve_parareal(tol=FIXED_TOL, allow_not_converged=True)
+        return timed_solve(FIXED_TOL)
+
+    # warm-up choices among configurations that reach the target error at the fixed rule:
+    # the coarse propagator, then inexact early iterations (mixed 1D only)
+    cands = {c: trial(c) for c in (["l1", "learned"] if args.coarse == "auto" else [args.coarse])}
+    ok = [c for c in cands if cands[c]["rel_err"] <= TARGET] or list(cands)
+    coarse = min(ok, key=lambda c: cands[c]["ms"])
     best = cands[coarse]
-    # inexact early iterations with the chosen coarse propagator (mixed 1D only)
     inexact, inexact_cand = 0.0, None
-    if args.inexact != "off" and args.precision == "mixed" and wl.specs[0].dim == 1:
+    if args.inexact != "off" and args.precision == "mixed" and not dim2:
         inexact_cand = {}
         for above in INEXACT_ABOVE:
-            c = tune(coarse, above)
+            c = trial(coarse, above)
             inexact_cand[f"{above:g}"] = c
-            if (args.inexact == "on" and inexact == 0.0) or c["ms"] < best["ms"]:
+            if c["rel_err"] <= TARGET and ((args.inexact == "on" and inexact == 0.0) or c["ms"] < best["ms"]):
                 inexact, best = above, c
-    pr.set_coarse(mlp if coarse == "learned" else None)
-    pr.set_inexact_fine(inexact)
-    tol = best["tol"]
+    configure(coarse, inexact)
+
+    # context only: the loosest increment tolerance that still reaches the target error,
+    # found with the reference solution (information the method itself does not have)
+    tol_t = 1.6e-7
+    while True:
+        pr.set_u0_dev(d_u0.data_ptr())
+        pr.solve_parareal(tol=tol_t, allow_not_converged=True)
+        if rel_err(pr.get_coeffs("parareal"), S) <= TARGET or tol_t < 1e-13:
+            break
+        tol_t /= 2.0
+    tuned = timed_solve(tol_t)
+    tol = FIXED_TOL
 
     # timed region: the solve runs as one CUDA graph (device-driven iteration loop)
     if not args.no_graph:
@@ -385,7 +512,8 @@ def main():
     pr.solve_parareal(tol=tol, allow_not_converged=True)
     torch.cuda.synchronize()
     st = pr.stats()
-    fine_ms, coarse_ms, fine_launches, flops = st["ms_fine"], st["ms_coarse"], st["iterations_max"], st["flop_fine"]
+    fine_ms, coarse_ms, flops_impl = st["ms_fine"], st["ms_coarse"], st["flop_fine"]
+    iters_host = pr.get_iterations()
     solve_ms_events = fine_ms + coarse_ms
     if not args.no_graph:
         pr.set_graph(True)
@@ -426,38 +554,53 @@ def main():
         uniform = {"ms": e0.elapsed_time(e1), "precision": args.precision,
                    "rel_gap_to_serial_hybrid": rel_err(pr.get_coeffs("serial"), S)}
 
-    # roofline of the dominant kernel (F stage), ALU-bound
+    # roofline of the dominant kernel (F stage).  1D: the algorithmic count of the
+    # step (alg_flops_step_1d) times the fine steps each launch processes; the
+    # library's own device counter of the work it did is kept beside it.  2D: the
+    # device counter (matrix-free operator applications, the algorithm in use).
+    fine_launches = int(iters_host.max())
     fine_avg_ms = fine_ms / max(fine_launches, 1)
-    achieved = flops / max(fine_launches, 1) / (fine_avg_ms * 1e-3) / 1e12
+    achieved_impl = flops_impl / max(fine_launches, 1) / (fine_avg_ms * 1e-3) / 1e12
     peak = fp64_tf if args.precision == "fp64" else fp32_tf
+    if dim2:
+        achieved, count = achieved_impl, "device counter of the implemented operator applications"
+    else:
+        alg, _ = fstage_alg_flops(wl, iters_host)
+        achieved = alg / max(fine_launches, 1) / (fine_avg_ms * 1e-3) / 1e12
+        count = ("4QK + 2Q(2K+1) + K^3/3 + 2K^2 per fine step (transforms, Toeplitz+Hankel moments, "
+                 "direct-solve count) x the fine steps of each launch")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_fstage",
+            "frac_impl": achieved_impl / peak, "traffic": None, "kernel": "k_fstage",
+            "launches": fine_launches, "ms_per_launch": fine_avg_ms,
             "share_of_solve": {"k_fstage": fine_ms / max(solve_ms_events, 1e-9),
                                "k_coarse_sweep": coarse_ms / max(solve_ms_events, 1e-9)},
-            "flops_source": "algorithmic FLOPs counted per step on the device (psl1_stats.flop_fine)",
+            "flops_source": count,
             "peak_source": ("measured FP64 FMA throughput (psl1_probe_peaks)" if args.precision == "fp64"
                             else "measured FP32 FMA throughput (psl1_probe_peaks)")}
 
     cpu = None
     if not args.no_cpu and dist.rank == 0 and dist.world == 1:
-        v, dt, ninst = oracle_throughput(wl, S, args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 oracle fine propagator F_n at n = P/2 of the first {ninst} instances "
-                         f"({dt:.1f} s, history from the GPU serial solve)"}
-        if wl.specs[0].dim == 2:
+        v, dt, ninst, thr = oracle_throughput(wl, S, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "host_cpus": os.cpu_count(),
+               "sample": f"FP64 oracle (OpenMP build) fine propagators F_n, n = P/2 .. P/2+{thr - 1}, one per "
+                         f"host thread, of the first {ninst} instances ({dt:.1f} s timed, history from the GPU "
+                         f"serial solve)"}
+        if dim2:
             cpu["sample"] = (f"FP64 oracle: {ninst} L1 steps of the instance with half the modes per axis "
-                             f"({dt:.1f} s), scaled by the oracle's K^2 Q cost to the full size")
+                             f"({dt:.1f} s), scaled by the oracle's K^2 Q cost to the full size, 1 thread")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": wl.name, "batch": wl.B, "P": wl.P, "precision": args.precision,
+                       "stop_rule": f"increment e_k <= {FIXED_TOL:g} (target error / 10, fixed in advance)",
                        "l2": "flushed (256 MB write) before every timed step",
                        "seed": wl.meta.get("seed", args.seed),
                        "execution": "host loop" if args.no_graph else "one CUDA graph per solve (device-driven loop)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "rel_err_vs_serial_fp64": err, "stop_tol": tol, "iterations": iters_all,
+            "tuned_tolerance": tuned,
             "coarse_propagator": coarse, "coarse_candidates": cands, "learned_training": train_info,
             "inexact_early_iterations": {"above": inexact, "candidates": inexact_cand},
             "serial_fp64_ms": serial_fp64_ms, "serial_ms": serial_ms, "serial_uniform": uniform,

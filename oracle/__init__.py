@@ -98,7 +98,7 @@ def lib(omp: bool = False):
             "orc_serial_uni": (ctypes.c_int, [pp, D_, D_]),
             "orc_coarse_sweep": (ctypes.c_int, [pp, D_, D_, D_, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, D_]),
-            "orc_fine_stage": (ctypes.c_int, [pp, D_, ctypes.c_int, D_]),
+            "orc_fine_stage": (ctypes.c_int, [pp, D_, ctypes.c_int, ctypes.c_int, D_]),
             "orc_threads": (ctypes.c_int, []),
             "orc_parareal": (ctypes.c_int, [pp, D_, ctypes.c_double, ctypes.c_int, D_, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_int, D_, D_, D_, P_]),
@@ -330,11 +330,13 @@ def parareal(p: Prob, u0, tol: float, max_iter: int | None = None, mlp=None, omp
     return Uall[: k + 1], err[:k], k
 
 
-def fine_stage(p: Prob, U, n0: int = 0, omp: bool = False):
-    """F_n(U_{0:n}) for n = n0..P-1 (rows n0.. of a P x K array; rows < n0 zero)."""
+def fine_stage(p: Prob, U, n0: int = 0, n1: int | None = None, omp: bool = False):
+    """F_n(U_{0:n}) for n = n0..n1-1 (rows of a P x K array; the other rows zero).
+    U holds at least U_0..U_{n1-1}."""
+    n1 = p.P if n1 is None else int(n1)
     U, pU = _d(U)
     F, pF = _out(p.P, p.K)
-    _chk(lib(omp).orc_fine_stage(ctypes.byref(p), pU, int(n0), pF), "fine_stage")
+    _chk(lib(omp).orc_fine_stage(ctypes.byref(p), pU, int(n0), n1, pF), "fine_stage")
     return F
 
 

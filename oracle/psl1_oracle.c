@@ -931,7 +931,7 @@ int orc_coarse_sweep(const orc_prob* p, const double* u0, double* U, const doubl
 }
 
 /* ------------------------------------------------------------------------ */
-/* Parallel stage of a parareal iteration: for every slice n >= n0,          */
+/* Parallel stage of a parareal iteration: for every slice n0 <= n < n1,    */
 /* G_old(n) = G_n(U_{0:n}) (when Gold is not NULL) and F_old(n) = F_n(U_{0:n}).*/
 /* The slices are independent, so the loop over n runs on all host threads  */
 /* when this file is compiled with OpenMP, as the paper runs its parallel    */
@@ -939,11 +939,11 @@ int orc_coarse_sweep(const orc_prob* p, const double* u0, double* U, const doubl
 /* pragma is ignored.  Each slice is computed the same way either way.       */
 /* ------------------------------------------------------------------------ */
 static int parallel_stage(const orc_prob* p, const orc_disc* d, const double* U, const orc_mlp* mp, int n0,
-                          double* Gold, double* Fold)
+                          int n1, double* Gold, double* Fold)
 {
-    int K = d->K, P = p->P, m = p->N / p->P, st = 0;
+    int K = d->K, m = p->N / p->P, st = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(min : st)
-    for (int n = n0; n < P; ++n) {
+    for (int n = n0; n < n1; ++n) {
         double* V = malloc(sizeof(double) * (size_t)(m + 1) * K);
         int sn = V ? 0 : -1000000;
         if (sn == 0 && Gold) sn = coarse_step(p, d, n, U, mp, Gold + (size_t)n * K);
@@ -955,13 +955,14 @@ static int parallel_stage(const orc_prob* p, const orc_disc* d, const double* U,
     return st;
 }
 
-/* F_n(U_{0:n}) of the slices n = n0..P-1 into Fold (row n), for timing the
- * parallel stage alone.                                                      */
-int orc_fine_stage(const orc_prob* p, const double* U, int n0, double* Fold)
+/* F_n(U_{0:n}) of the slices n = n0..n1-1 into Fold (row n), for timing
+ * the parallel stage alone.                                                  */
+int orc_fine_stage(const orc_prob* p, const double* U, int n0, int n1, double* Fold)
 {
     orc_disc d;
+    if (n0 < 0 || n1 > p->P || n0 > n1) return -2;
     if (disc_build(p, &d)) return -1;
-    int st = parallel_stage(p, &d, U, NULL, n0, NULL, Fold);
+    int st = parallel_stage(p, &d, U, NULL, n0, n1, NULL, Fold);
     disc_free(&d);
     return st;
 }
@@ -1016,7 +1017,7 @@ int orc_parareal(const orc_prob* p, const double* u0, double tol, int max_iter,
         const double* Uk = Uall + (size_t)k * slab;
         double* Uk1 = Uall + (size_t)(k + 1) * slab;
         /* parallel stage (the slices are independent given U^k) */
-        st = parallel_stage(p, &d, Uk, mp, 0, Gold, Fold);
+        st = parallel_stage(p, &d, Uk, mp, 0, P, Gold, Fold);
         if (st) break;
         /* sequential coarse sweep with correction */
         memcpy(Uk1, u0, sizeof(double) * K);

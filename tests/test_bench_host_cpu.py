@@ -1,7 +1,8 @@
 """Host logic of bench.py that decides whether a measurement is valid, on CPU:
 the clock sampler's parsing of nvidia-smi rows (median SM clock under load,
-the maximum clock, and the throttle reasons seen), and the relative-error
-measure the headline is gated on."""
+the maximum clock, and the throttle reasons seen), the relative-error
+measure the headline is gated on, the algorithmic FLOP count of the roofline,
+and the reference arm's whole oracle solves of the small configurations."""
 import os
 import sys
 
@@ -54,3 +55,21 @@ def test_rel_err_is_max_over_instances_of_normwise_error():
     U = [S[0] + np.array([[0.0, 0.0], [0.3, 0.4]]), S[1] + np.array([[0.0, 0.05]])]
     # instance 0: max_n ||dU_n|| / max_n ||S_n|| = 0.5 / 5; instance 1: 0.05 / 1
     assert bench.rel_err(U, S) == 0.1
+
+
+def test_algorithmic_count_of_the_step_and_of_a_solve():
+    # K = 3, Q = 6: 4 Q K + 2 Q (2K+1) + K^3/3 + 2K^2 = 72 + 84 + 9 + 18
+    assert bench.alg_flops_step_1d(3, 6) == 183.0
+    from paper_2510_11023_gb300 import workloads
+    wl = workloads.small_batch(B=2, P=4)   # K = 7 (m = 3), 33 (m = 2)
+    # instance 0: 2 iterations -> slices 4 + 3; instance 1: 3 iterations -> 4 + 3 + 2
+    tot, launches = bench.fstage_alg_flops(wl, [2, 3])
+    ref = 7 * 3 * bench.alg_flops_step_1d(7, 14) + 9 * 2 * bench.alg_flops_step_1d(33, 66)
+    assert launches == 3 and abs(tot - ref) <= 1e-9 * ref
+
+
+def test_reference_arm_context_timings_of_the_small_configurations():
+    out = bench.oracle_paper_shapes()
+    for r in out.values():
+        assert r["serial_uniform_s"] > 0 and r["serial_hybrid_s"] > 0 and r["parareal_iterations"] >= 1
+        assert any(k.startswith("parareal_s_threads") for k in r)
