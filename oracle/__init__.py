@@ -99,6 +99,10 @@ def lib(omp: bool = False):
             "orc_coarse_sweep": (ctypes.c_int, [pp, D_, D_, D_, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, D_]),
             "orc_fine_stage": (ctypes.c_int, [pp, D_, ctypes.c_int, ctypes.c_int, D_]),
+            "orc_gauss_jacobi": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, D_, D_]),
+            "orc_soe_nodes": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_int, D_, D_]),
+            "orc_serial_uni_soe": (ctypes.c_int, [pp, D_, ctypes.c_int, ctypes.c_double, D_]),
             "orc_threads": (ctypes.c_int, []),
             "orc_parareal": (ctypes.c_int, [pp, D_, ctypes.c_double, ctypes.c_int, D_, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_int, D_, D_, D_, P_]),
@@ -292,6 +296,34 @@ def serial_uni(p: Prob, u0):
     u0, pu = _d(u0)
     W, pW = _out(p.N + 1, p.K)
     _chk(lib().orc_serial_uni(ctypes.byref(p), pu, pW), "serial_uni")
+    return W
+
+
+SOE_NLOC = 16      # steps of the exact local window of the fast history
+SOE_EPS = 1e-12    # relative accuracy the exponentials are built for
+
+
+def gauss_jacobi(n: int, ja: float, jb: float):
+    """Gauss-Jacobi nodes and weights for (1-t)^ja (1+t)^jb on (-1, 1)."""
+    (t, pt), (w, pw) = _out(n), _out(n)
+    _chk(lib().orc_gauss_jacobi(int(n), float(ja), float(jb), pt, pw), "gauss_jacobi")
+    return t, w
+
+
+def soe_nodes(alpha: float, X: int, nloc: int = SOE_NLOC, eps: float = SOE_EPS):
+    """Exponents s and weights w with b(x) ~ sum_i w_i exp(-s_i x) on [nloc, X]."""
+    (s, ps), (w, pw) = _out(512), _out(512)
+    L = lib().orc_soe_nodes(float(alpha), int(nloc), int(X), float(eps), 512, ps, pw)
+    if L < 0:
+        raise OracleError("soe_nodes failed")
+    return s[:L], w[:L]
+
+
+def serial_uni_soe(p: Prob, u0, nloc: int = SOE_NLOC, eps: float = SOE_EPS):
+    """The uniform L1 scheme with the sum-of-exponentials weights: (N+1) x K."""
+    u0, pu = _d(u0)
+    W, pW = _out(p.N + 1, p.K)
+    _chk(lib().orc_serial_uni_soe(ctypes.byref(p), pu, int(nloc), float(eps), pW), "serial_uni_soe")
     return W
 
 

@@ -1074,3 +1074,169 @@ double orc_l1_hybrid(double alpha, double dT, int M, int n, int r, const double*
     for (int j = 1; j <= r; ++j) sf += orc_b(alpha, (double)(r - j)) * (yf[j] - yf[j - 1]);
     return (pow(dT, -alpha) * sc + pow(dt, -alpha) * sf) / orc_gamma2a(alpha);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Fast history by a sum of exponentials (the paper's outlook, Conclusion    */
+/* item (i): a fast evaluation of the nonlocal memory term).  The paper gives */
+/* no construction; the reading used here approximates the L1 weights        */
+/*   b(x) = (x+1)^{1-a} - x^{1-a} = (1-a) int_x^{x+1} s^{-a} ds               */
+/* for x >= nloc through the Laplace-transform integral                      */
+/*   s^{-a} = 1/Gamma(a) int_0^inf tau^{a-1} e^{-s tau} dtau,                 */
+/* i.e. b(x) = c int_0^inf tau^{a-2} (1 - e^{-tau}) e^{-x tau} dtau,          */
+/* c = (1-a)/Gamma(a), discretised (the published Gauss-Jacobi / Gauss-      */
+/* Legendre construction of sum-of-exponentials kernels) as                   */
+/*   [0, tau0], tau0 = 1/X: Gauss-Jacobi with weight tau^{a-1}, 10 nodes;     */
+/*   [tau0, tau1] in y = log tau: composite Gauss-Legendre, 14 nodes on each  */
+/*     of ceil((y1 - y0)/2) equal segments, y1 = log(log(1/eps)/nloc) + 0.3,  */
+/* giving b(x) ~ sum_i w_i e^{-s_i x} on [nloc, X] to ~1e-14 relative.        */
+/* The scheme with the approximated weights is the uniform L1 scheme with     */
+/*   bt(x) = b(x) for x < nloc,  sum_i w_i e^{-s_i x} for x >= nloc.           */
+/* alpha = 1: c = 0, no exponentials (no history).                           */
+/* ------------------------------------------------------------------------ */
+#define SOE_GJ 10
+#define SOE_GL 14
+
+/* Eigenvalues and eigenvectors of a symmetric n x n matrix by cyclic Jacobi
+ * rotations (A is overwritten; V receives the eigenvectors as columns).    */
+static void jacobi_eigen(int n, double* A, double* V)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i * n + j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+        if (off < 1e-300) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {   /* A <- A J */
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = cs * akp - sn * akq;
+                    A[k * n + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {   /* A <- J^T A */
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = cs * apk - sn * aqk;
+                    A[q * n + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < n; ++k) {   /* V <- V J */
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = cs * vkp - sn * vkq;
+                    V[k * n + q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+}
+
+/* Gauss-Jacobi rule for the weight (1-t)^ja (1+t)^jb on (-1,1) by the
+ * Golub-Welsch construction: nodes = eigenvalues of the Jacobi matrix of the
+ * monic three-term recurrence, weights = mu0 (first eigenvector component)^2,
+ * mu0 = 2^{ja+jb+1} Gamma(ja+1) Gamma(jb+1) / Gamma(ja+jb+2).               */
+int orc_gauss_jacobi(int n, double ja, double jb, double* t, double* w)
+{
+    double* A = calloc((size_t)n * n, sizeof(double));
+    double* V = malloc(sizeof(double) * (size_t)n * n);
+    if (!A || !V) { free(A); free(V); return -1; }
+    for (int k = 0; k < n; ++k) {
+        double s = 2.0 * k + ja + jb;
+        A[k * n + k] = k == 0 ? (jb - ja) / (ja + jb + 2.0) : (jb * jb - ja * ja) / (s * (s + 2.0));
+        if (k >= 1) {
+            double beta = 4.0 * k * (k + ja) * (k + jb) * (k + ja + jb) / (s * s * (s + 1.0) * (s - 1.0));
+            A[k * n + k - 1] = A[(k - 1) * n + k] = sqrt(beta);
+        }
+    }
+    jacobi_eigen(n, A, V);
+    double mu0 = pow(2.0, ja + jb + 1.0) * tgamma(ja + 1.0) * tgamma(jb + 1.0) / tgamma(ja + jb + 2.0);
+    for (int i = 0; i < n; ++i) {   /* ascending order by selection */
+        t[i] = A[i * n + i];
+        w[i] = mu0 * V[i] * V[i];
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (t[j] < t[i]) {
+                double x = t[i]; t[i] = t[j]; t[j] = x;
+                x = w[i]; w[i] = w[j]; w[j] = x;
+            }
+    free(A); free(V);
+    return 0;
+}
+
+/* Exponents s_i and weights w_i of the approximation above for the window
+ * [nloc, X]; returns their number (<= maxn), or -1.                         */
+int orc_soe_nodes(double alpha, int nloc, int X, double eps, int maxn, double* s, double* w)
+{
+    if (alpha >= 1.0) return 0;
+    double c = (1.0 - alpha) / tgamma(alpha);
+    double tau0 = 1.0 / X;
+    double y0 = log(tau0), y1 = log(log(1.0 / eps) / nloc) + 0.3;
+    int nseg = (int)ceil((y1 - y0) / 2.0);
+    if (nseg < 1) nseg = 1;
+    int L = SOE_GJ + nseg * SOE_GL;
+    if (L > maxn) return -1;
+    double t[SOE_GJ], wt[SOE_GJ];
+    if (orc_gauss_jacobi(SOE_GJ, 0.0, alpha - 1.0, t, wt)) return -1;
+    for (int i = 0; i < SOE_GJ; ++i) {
+        /* tau = tau0 (1+t)/2: tau^{a-1} dtau = (tau0/2)^a (1+t)^{a-1} dt */
+        double tau = tau0 * (1.0 + t[i]) / 2.0;
+        s[i] = tau;
+        w[i] = c * pow(tau0 / 2.0, alpha) * wt[i] * (-expm1(-tau)) / tau;
+    }
+    double xg[SOE_GL], wg[SOE_GL];
+    orc_gauss_legendre(SOE_GL, xg, wg);   /* on (0,1) */
+    double hseg = (y1 - y0) / nseg;
+    for (int g = 0; g < nseg; ++g)
+        for (int i = 0; i < SOE_GL; ++i) {
+            double y = y0 + hseg * (g + xg[i]);
+            double tau = exp(y);
+            int k = SOE_GJ + g * SOE_GL + i;
+            s[k] = tau;
+            w[k] = c * hseg * wg[i] * exp((alpha - 1.0) * y) * (-expm1(-tau));
+        }
+    return L;
+}
+
+/* The uniform L1 scheme (as orc_serial_uni, in the difference form
+ *   hist_j = W_j - sum_{l=0}^{j-1} bt(j-l) (W_{l+1} - W_l))
+ * with the weights bt of the approximation above, nloc, eps given and the
+ * window [nloc, N].  W: (N+1) x K.                                          */
+int orc_serial_uni_soe(const orc_prob* p, const double* u0, int nloc, double eps, double* W)
+{
+    int N = p->N, st = 0;
+    double s[512], w[512];
+    int L = orc_soe_nodes(p->alpha, nloc, N, eps, 512, s, w);
+    if (L < 0) return -2;
+    double* bt = malloc(sizeof(double) * (N + 1));
+    if (!bt) return -1000000;
+    for (int x = 0; x <= N; ++x) {
+        if (x < nloc) {
+            bt[x] = orc_b(p->alpha, (double)x);
+        } else {
+            double v = 0.0;
+            for (int i = 0; i < L; ++i) v += w[i] * exp(-s[i] * x);
+            bt[x] = v;
+        }
+    }
+    orc_disc d;
+    if (disc_build(p, &d)) { free(bt); return -1; }
+    int K = d.K;
+    double a = p->alpha, dt = p->T / N;
+    double mu = pow(dt, a) * orc_gamma2a(a);
+    double* hist = malloc(sizeof(double) * K);
+    if (!hist) { free(bt); disc_free(&d); return -1000000; }
+    memcpy(W, u0, sizeof(double) * K);
+    for (int j = 0; j < N && st == 0; ++j) {
+        for (int i = 0; i < K; ++i) hist[i] = W[(size_t)j * K + i];
+        for (int l = 0; l < j; ++l)
+            for (int i = 0; i < K; ++i)
+                hist[i] -= bt[j - l] * (W[(size_t)(l + 1) * K + i] - W[(size_t)l * K + i]);
+        st = step_solve(p, &d, W + (size_t)j * K, dt * j, mu, hist, W + (size_t)(j + 1) * K);
+    }
+    free(hist); free(bt);
+    disc_free(&d);
+    return st;
+}

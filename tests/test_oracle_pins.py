@@ -364,8 +364,9 @@ def test_openmp_parallel_stage_is_the_same_computation():
     U2, e2, k2 = O.parareal(p, u0, 1e-12, omp=True)
     assert k1 == k2 and np.array_equal(U1, U2) and np.array_equal(e1, e2)
     assert np.array_equal(O.fine_stage(p, U1[0], 2), O.fine_stage(p, U1[0], 2, omp=True))
-    F = O.fine_stage(p, U1[0], 2)
-    assert np.array_equal(F[3], O.fine_slice(p, 3, U1[0][:4])[-1]) and not F[:2].any()
+    F = O.fine_stage(p, U1[0], 2, 5)
+    assert np.array_equal(F[3], O.fine_slice(p, 3, U1[0][:4])[-1])
+    assert not F[:2].any() and not F[5:].any() and F[2:5].all()
 
 
 def test_fine_propagator_expanded_equals_difference_form():
@@ -610,3 +611,37 @@ def test_mlp_features_definition():
     eta = O.b(0.5, 2) * (U[1] - U[0]) + O.b(0.5, 1) * (U[2] - U[1])
     assert np.abs(z[6:9] - k2[:3] * eta[:3]).max() < 1e-15
     assert z[9] == 0.5 and abs(z[10] - 0.5) < 1e-15
+
+
+# ---------------------------------------------------------------- fast history (sum of exponentials)
+@pytest.mark.parametrize("alpha", [0.2, 0.5, 0.9])
+def test_gauss_jacobi_against_scipy(alpha):
+    from scipy.special import roots_jacobi
+    t, w = O.gauss_jacobi(10, 0.0, alpha - 1.0)
+    t2, w2 = roots_jacobi(10, 0.0, alpha - 1.0)
+    assert np.abs(t - t2).max() < 1e-13 and np.abs(w - w2).max() < 1e-12 * w2.max()
+
+
+@pytest.mark.parametrize("alpha", [0.2, 0.5, 0.9, 0.99])
+@pytest.mark.parametrize("X", [17, 1024, 8192])
+def test_soe_approximates_l1_weights(alpha, X):
+    # b(x) = x^{1-a} ((1 + 1/x)^{1-a} - 1) written without cancellation (expm1, log1p)
+    s, w = O.soe_nodes(alpha, X)
+    x = np.arange(O.SOE_NLOC, X + 1, dtype=np.float64)
+    ref = x ** (1 - alpha) * np.expm1((1 - alpha) * np.log1p(1 / x))
+    approx = (w[None, :] * np.exp(-np.outer(x, s))).sum(1)
+    assert np.abs(approx / ref - 1).max() < 1e-13
+    assert len(s) <= 80 and np.all(s > 0) and np.all(w > 0)
+
+
+def test_soe_uniform_scheme_matches_exact_history():
+    # the scheme with the approximated weights stays within rounding of the exact
+    # uniform scheme; alpha = 1 has no history (no exponentials) and N < nloc
+    # uses only the exact local window
+    rng = np.random.default_rng(4)
+    for K, N, a in ((12, 200, 0.4), (8, 100, 0.8), (12, 64, 1.0), (9, 15, 0.5)):
+        p = O.make_prob(Mx=K, N=N, P=1, alpha=a, dpar=CFG1_D, fpar=CFG1_F)
+        u0 = rng.standard_normal(K) / np.arange(1, K + 1) ** 2
+        W, Ws = O.serial_uni(p, u0), O.serial_uni_soe(p, u0)
+        assert np.abs(Ws - W).max() < 1e-13 * np.abs(W).max(), (K, N, a)
+    assert len(O.soe_nodes(1.0, 100)[0]) == 0
