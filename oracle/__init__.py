@@ -39,11 +39,13 @@ class Prob(ctypes.Structure):
         ("alpha", ctypes.c_double), ("T", ctypes.c_double),
         ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2),
         ("dpar", ctypes.c_double * 8), ("fpar", ctypes.c_double * 8),
-        ("solver", ctypes.c_int),
+        ("solver", ctypes.c_int), ("basis", ctypes.c_int),
     ]
 
     @property
     def K(self) -> int:
+        if self.basis == 1:
+            return self.Mx - 1
         return self.Mx * (self.My if self.dim == 2 else 1)
 
     @property
@@ -89,6 +91,7 @@ def lib(omp: bool = False):
             "orc_stiffness": (ctypes.c_int, [pp, D_, D_]),
             "orc_load": (ctypes.c_int, [pp, D_, D_]),
             "orc_apply_stiffness": (ctypes.c_int, [pp, D_, D_, D_]),
+            "orc_cheb": (ctypes.c_int, [pp, D_, D_]),
             "orc_project": (ctypes.c_int, [pp, D_, D_]),
             "orc_chol_solve": (ctypes.c_int, [ctypes.c_int, D_, D_, D_]),
             "orc_step": (ctypes.c_int, [pp, D_, ctypes.c_double, ctypes.c_double, D_, D_]),
@@ -147,11 +150,13 @@ def _out(*shape):
 
 def make_prob(*, dim=1, Mx, My=1, Qx=None, Qy=None, N, P, alpha, T=1.0, lo=(0.0, 0.0),
               hi=(1.0, 1.0), dpar=(1.0, 0.5, 0, 0, 0, 0, 0, 0), fpar=(0.1, 0, 0, 0, 0, 0, 0, 0),
-              solver: str = "cholesky") -> Prob:
+              solver: str = "cholesky", basis: str = "sine") -> Prob:
     """Problem record; Qx/Qy default to twice the modes (Gauss-Legendre).
     solver: "cholesky" (dense factor of the assembled matrix) or "cg"
     (conjugate gradients on the weak form, for mode counts whose assembly
-    is out of reach); both solve the same SPD system of each step."""
+    is out of reach); both solve the same SPD system of each step.
+    basis: "sine" (Galerkin, Mx modes) or "cheb" (Chebyshev-Lobatto
+    collocation, 1D: Mx intervals, the Mx - 1 interior nodal values)."""
     p = Prob()
     p.dim, p.Mx = dim, Mx
     p.My = My if dim == 2 else 1
@@ -165,6 +170,9 @@ def make_prob(*, dim=1, Mx, My=1, Qx=None, Qy=None, N, P, alpha, T=1.0, lo=(0.0,
     for i in range(8):
         p.dpar[i], p.fpar[i] = dp[i], fp[i]
     p.solver = {"cholesky": 0, "cg": 1}[solver]
+    p.basis = {"sine": 0, "cheb": 1}[basis]
+    if p.basis == 1 and dim != 1:
+        raise ValueError("collocation is 1D")
     if N % P:
         raise ValueError("P must divide N")
     return p
@@ -225,6 +233,14 @@ def stiffness(p: Prob, Dq):
     A, pA = _out(p.K, p.K)
     _chk(lib().orc_stiffness(ctypes.byref(p), pD, pA), "stiffness")
     return A
+
+
+def cheb(p: Prob):
+    """Chebyshev-Lobatto nodes x_0..x_n (x_0 = hi) and the differentiation matrix."""
+    n = p.Mx
+    (x, px), (Dm, pD) = _out(n + 1), _out(n + 1, n + 1)
+    _chk(lib().orc_cheb(ctypes.byref(p), px, pD), "cheb")
+    return x, Dm
 
 
 def apply_stiffness(p: Prob, Dq, v):

@@ -63,6 +63,8 @@ typedef struct {
     double fpar[8];
     int solver;         /* step solve: 0 dense Cholesky of the assembled matrix,
                            1 conjugate gradients on the weak form (no matrix) */
+    int basis;          /* space: 0 sine Galerkin (Mx modes), 1 Chebyshev-Lobatto
+                           collocation (1D, Mx intervals, Mx - 1 interior values) */
 } orc_prob;
 
 /* ------------------------------------------------------------------------ */
@@ -130,6 +132,7 @@ typedef struct {
     double *xq, *yq, *wq;   /* Q */
     double *phi;            /* Q x K */
     double *gx, *gy;        /* Q x K gradient components (gy unused in 1D) */
+    double *Dm;             /* collocation: Q x Q differentiation matrix (Q = Mx + 1 nodes) */
 } orc_disc;
 
 static void sine1d(int M, double lo, double hi, double x, double* v, double* dv)
@@ -142,8 +145,50 @@ static void sine1d(int M, double lo, double hi, double x, double* v, double* dv)
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Chebyshev-Lobatto collocation (Sec. 4.1, the paper's own implementation): */
+/* nodes x_j = (a+b)/2 + (b-a)/2 cos(j pi / n), j = 0..n, and the first-      */
+/* derivative matrix (Eq. in Sec. 4.1)                                       */
+/*   D_ij = (c_i/c_j) (-1)^{i+j} / (xi_i - xi_j), i != j,  c_0 = c_n = 2,     */
+/*   D_ii = -sum_{m != i} D_im  (the negative-sum form the paper gives),     */
+/* on the reference nodes xi, scaled by 2/(b-a) on [a,b].  The unknowns are  */
+/* the values at the interior nodes j = 1..n-1 (u = 0 at j = 0, n).          */
+/* ------------------------------------------------------------------------ */
+static int disc_build_cheb(const orc_prob* p, orc_disc* d)
+{
+    int n = p->Mx;
+    memset(d, 0, sizeof *d);
+    d->K = n - 1;
+    d->Q = n + 1;
+    d->xq = malloc(sizeof(double) * (n + 1));
+    d->Dm = malloc(sizeof(double) * (size_t)(n + 1) * (n + 1));
+    double* xi = malloc(sizeof(double) * (n + 1));
+    if (!d->xq || !d->Dm || !xi) { free(xi); return -1; }
+    double a = p->lo[0], b = p->hi[0];
+    for (int j = 0; j <= n; ++j) {
+        xi[j] = cos(j * M_PI / n);
+        d->xq[j] = 0.5 * (a + b) + 0.5 * (b - a) * xi[j];
+    }
+    for (int i = 0; i <= n; ++i) {
+        double ci = (i == 0 || i == n) ? 2.0 : 1.0, row = 0.0;
+        for (int j = 0; j <= n; ++j) {
+            if (j == i) continue;
+            double cj = (j == 0 || j == n) ? 2.0 : 1.0;
+            double v = (ci / cj) * (((i + j) % 2) ? -1.0 : 1.0) / (xi[i] - xi[j]);
+            d->Dm[(size_t)i * (n + 1) + j] = v;
+            row += v;
+        }
+        d->Dm[(size_t)i * (n + 1) + i] = -row;
+    }
+    for (int e = 0; e < (n + 1) * (n + 1); ++e) d->Dm[e] *= 2.0 / (b - a);
+    free(xi);
+    return 0;
+}
+
 static int disc_build(const orc_prob* p, orc_disc* d)
 {
+    if (p->basis == 1) return disc_build_cheb(p, d);
+    d->Dm = NULL;
     int My = p->dim == 1 ? 1 : p->My, Qy = p->dim == 1 ? 1 : p->Qy;
     d->K = p->Mx * My;
     d->Q = p->Qx * Qy;
@@ -189,7 +234,7 @@ static int disc_build(const orc_prob* p, orc_disc* d)
 
 static void disc_free(orc_disc* d)
 {
-    free(d->xq); free(d->yq); free(d->wq); free(d->phi); free(d->gx); free(d->gy);
+    free(d->xq); free(d->yq); free(d->wq); free(d->phi); free(d->gx); free(d->gy); free(d->Dm);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -434,9 +479,70 @@ out:
     return st;
 }
 
+/* Gaussian elimination with partial pivoting: solves M x = r (M, r overwritten).
+ * Returns 0, or -(j+1) if column j has no nonzero pivot.                    */
+static int lu_solve(int K, double* M, double* r, double* x)
+{
+    for (int j = 0; j < K; ++j) {
+        int piv = j;
+        for (int i = j + 1; i < K; ++i)
+            if (fabs(M[(size_t)i * K + j]) > fabs(M[(size_t)piv * K + j])) piv = i;
+        if (!(fabs(M[(size_t)piv * K + j]) > 0.0)) return -(j + 1);
+        if (piv != j) {
+            for (int k = 0; k < K; ++k) {
+                double t = M[(size_t)j * K + k];
+                M[(size_t)j * K + k] = M[(size_t)piv * K + k];
+                M[(size_t)piv * K + k] = t;
+            }
+            double t = r[j]; r[j] = r[piv]; r[piv] = t;
+        }
+        for (int i = j + 1; i < K; ++i) {
+            double l = M[(size_t)i * K + j] / M[(size_t)j * K + j];
+            for (int k = j; k < K; ++k) M[(size_t)i * K + k] -= l * M[(size_t)j * K + k];
+            r[i] -= l * r[j];
+        }
+    }
+    for (int i = K - 1; i >= 0; --i) {
+        double s = r[i];
+        for (int k = i + 1; k < K; ++k) s -= M[(size_t)i * K + k] * x[k];
+        x[i] = s / M[(size_t)i * K + i];
+    }
+    return 0;
+}
+
+/* The collocation step (Eq. NumericalSchemeMainSystem): with the diffusivity
+ * at every node, Dc_j = D(x_j, t_e, u_j) (u_j = c_{j-1} inside, 0 on the
+ * boundary), and N_ik = sum_j Dm_ij Dc_j Dm_jk for interior i, k (the discrete
+ * div(D grad) of Sec. 4.1 restricted to the interior unknowns), solve
+ *   (I - mu N) c_new = hist + mu f(x_I, t_e, c).                            */
+static int step_solve_cheb(const orc_prob* p, const orc_disc* d, const double* cprev, double te,
+                           double mu, const double* hist, double* cnew)
+{
+    int K = d->K, Q = d->Q, st;
+    double* u = malloc(sizeof(double) * Q);
+    double* Dc = malloc(sizeof(double) * Q);
+    double* M = malloc(sizeof(double) * (size_t)K * K);
+    double* r = malloc(sizeof(double) * K);
+    if (!u || !Dc || !M || !r) { st = -1000000; goto out; }
+    for (int j = 0; j < Q; ++j) u[j] = (j == 0 || j == Q - 1) ? 0.0 : cprev[j - 1];
+    for (int j = 0; j < Q; ++j) Dc[j] = orc_D(p, d->xq[j], 0.0, te, u[j]);
+    for (int i = 0; i < K; ++i)
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+            for (int j = 0; j < Q; ++j) s += d->Dm[(size_t)(i + 1) * Q + j] * Dc[j] * d->Dm[(size_t)j * Q + k + 1];
+            M[(size_t)i * K + k] = (i == k ? 1.0 : 0.0) - mu * s;
+        }
+    for (int i = 0; i < K; ++i) r[i] = hist[i] + mu * orc_f(p, d->xq[i + 1], 0.0, te, u[i + 1]);
+    st = lu_solve(K, M, r, cnew);
+out:
+    free(u); free(Dc); free(M); free(r);
+    return st;
+}
+
 static int step_solve(const orc_prob* p, const orc_disc* d, const double* cprev, double te,
                       double mu, const double* hist, double* cnew)
 {
+    if (p->basis == 1) return step_solve_cheb(p, d, cprev, te, mu, hist, cnew);
     if (p->solver == 1) return step_solve_cg(p, d, cprev, te, mu, hist, cnew);
     int K = d->K, Q = d->Q, st;
     double* uq = malloc(sizeof(double) * Q);
@@ -496,6 +602,17 @@ int orc_stiffness(const orc_prob* p, const double* Dq, double* A)
     orc_disc d;
     if (disc_build(p, &d)) return -1;
     stiffness(p, &d, Dq, A);
+    disc_free(&d);
+    return 0;
+}
+
+/* Collocation nodes (Mx + 1) and differentiation matrix ((Mx+1)^2, row-major). */
+int orc_cheb(const orc_prob* p, double* x, double* Dm)
+{
+    orc_disc d;
+    if (p->basis != 1 || disc_build(p, &d)) return -1;
+    memcpy(x, d.xq, sizeof(double) * d.Q);
+    memcpy(Dm, d.Dm, sizeof(double) * (size_t)d.Q * d.Q);
     disc_free(&d);
     return 0;
 }

@@ -645,3 +645,95 @@ def test_soe_uniform_scheme_matches_exact_history():
         W, Ws = O.serial_uni(p, u0), O.serial_uni_soe(p, u0)
         assert np.abs(Ws - W).max() < 1e-13 * np.abs(W).max(), (K, N, a)
     assert len(O.soe_nodes(1.0, 100)[0]) == 0
+
+
+# ---------------------------------------------------------------- Chebyshev-Lobatto collocation (Sec. 4.1)
+def test_collocation_differentiation_matrix():
+    # exact on polynomials of degree <= n (Sec. 4.1: D u = u' for the interpolant), and the
+    # negative-sum diagonal equals the explicit form the paper prints, scaled by 2/(b-a)
+    n, a, b = 12, 0.2, 1.7
+    p = O.make_prob(Mx=n, N=4, P=1, alpha=0.5, basis="cheb", lo=(a, 0), hi=(b, 1))
+    x, Dm = O.cheb(p)
+    xi = np.cos(np.arange(n + 1) * math.pi / n)
+    assert np.abs(x - ((a + b) / 2 + (b - a) / 2 * xi)).max() < 1e-15
+    for k in range(n + 1):
+        d = k * x ** (k - 1) if k else 0 * x
+        assert np.abs(Dm @ x**k - d).max() < 1e-13 * max(1.0, np.abs(d).max()), k
+    sc = 2.0 / (b - a)
+    diag = np.r_[(2 * n * n + 1) / 6, -xi[1:-1] / (2 * (1 - xi[1:-1] ** 2)), -(2 * n * n + 1) / 6] * sc
+    assert np.abs(np.diag(Dm) - diag).max() < 1e-12 * np.abs(diag).max()
+
+
+def test_collocation_step_is_polynomial_exact():
+    # D = d0, f = 0: (I - mu d0 D^2) u = rhs has the polynomial solution p whenever
+    # rhs = p - mu d0 p'' at the interior nodes and deg p <= n, p(0) = p(1) = 0
+    n, d0, mu = 10, 1.3, 0.05
+    p = O.make_prob(Mx=n, N=4, P=1, alpha=0.5, basis="cheb", dpar=(d0, 0, 0, 0), fpar=(0,))
+    x, _ = O.cheb(p)
+    xi = x[1:-1]
+    pv = xi**2 * (1 - xi) ** 2 * (1 + xi)
+    # p = x^2 - x^3 - x^4 + x^5 ... expanded: x^2 (1 - 2x + x^2)(1 + x) = x^2 - x^3 - x^4 + x^5
+    p2 = 2 - 6 * xi - 12 * xi**2 + 20 * xi**3
+    got = O.step(p, np.zeros(n - 1), 0.0, mu, pv - mu * d0 * p2)
+    assert np.abs(got - pv).max() < 1e-13
+
+
+def _cheb_D_numpy(n, a, b):
+    # independent construction: derivative of each Lagrange basis polynomial of the
+    # nodes, fitted exactly by numpy's Chebyshev series and differentiated there
+    from numpy.polynomial import chebyshev as C
+    xi = np.cos(np.arange(n + 1) * math.pi / n)
+    D = np.zeros((n + 1, n + 1))
+    for j in range(n + 1):
+        e = np.zeros(n + 1)
+        e[j] = 1.0
+        c = C.chebfit(xi, e, n)
+        D[:, j] = C.chebval(xi, C.chebder(c)) * 2.0 / (b - a)
+    return (a + b) / 2 + (b - a) / 2 * xi, D
+
+
+def test_collocation_alpha_one_is_backward_euler_numpy():
+    # alpha = 1: the uniform scheme is linearly-implicit backward Euler of
+    # u_t = (D(u) u_x)_x + f, written here with numpy (independent matrices and solve)
+    n, N = 10, 20
+    dp, fp = (1.0, 0, 1.0, 0, 0.2), (0, 0, 0, 1.0)      # D = (1 + u)(1 + 0.2 sin 2 pi x), f = sin(pi x) e^{-t}
+    p = O.make_prob(Mx=n, N=N, P=1, alpha=1.0, basis="cheb", dpar=dp, fpar=fp)
+    x, Dn = _cheb_D_numpy(n, 0.0, 1.0)
+    u = 0.3 * np.sin(math.pi * x[1:-1])
+    W = O.serial_uni(p, u)
+    dt = 1.0 / N
+    for j in range(N):
+        full = np.r_[0.0, u, 0.0]
+        Dc = (1 + full) * (1 + 0.2 * np.sin(2 * math.pi * x))
+        Nm = (Dn @ np.diag(Dc) @ Dn)[1:-1, 1:-1]
+        f = np.sin(math.pi * x[1:-1]) * math.exp(-j * dt)
+        u = np.linalg.solve(np.eye(n - 1) - dt * Nm, u + dt * f)
+        assert np.abs(W[j + 1] - u).max() < 1e-12, j
+
+
+def test_collocation_spectral_convergence_manufactured():
+    # u = (1 + t^2) sin(pi x)/(2 - cos pi x), D = 1 + 0.5 sin(pi x), source S2: the
+    # error at t = T falls geometrically in n until the time-discretisation floor
+    errs = []
+    for n in (6, 8, 12):
+        p = O.make_prob(Mx=n, N=64, P=1, alpha=0.5, T=0.01, basis="cheb", dpar=(1.0, 0, 0, 0.5),
+                        fpar=(0, 0, 0, 0, 0, 1.0))
+        x, _ = O.cheb(p)
+        xi = x[1:-1]
+        s = np.sin(math.pi * xi) / (2 - np.cos(math.pi * xi))
+        errs.append(np.abs(O.serial_uni(p, s)[-1] - (1 + 0.01**2) * s).max())
+    assert errs[0] > 10 * errs[1] > 10 * errs[2] and errs[2] < 1e-5
+
+
+def test_collocation_parareal_finite_termination_paper_shape():
+    # the paper's model problem (D = 1 + u, f = sin(pi x) e^{-t}, u0 = x^4 (1-x)^4, alpha
+    # = 0.5) on 2^4 intervals: after k iterations U^k_{0:k} is the sequential F sweep
+    n, P, m = 16, 8, 4
+    p = O.make_prob(Mx=n, N=P * m, P=P, alpha=0.5, basis="cheb", dpar=(1.0, 0, 1.0, 0), fpar=(0, 0, 0, 1.0))
+    x, _ = O.cheb(p)
+    u0 = x[1:-1] ** 4 * (1 - x[1:-1]) ** 4
+    U, _, k = O.parareal(p, u0, tol=0.0)
+    S = O.serial_hyb(p, u0)
+    assert k == P
+    for j in range(k + 1):
+        assert np.abs(U[j][: j + 1] - S[: j + 1]).max() <= 1e-13 * np.abs(S).max(), j
