@@ -73,8 +73,16 @@ enum { PSL1_PREC_FP64 = 0, PSL1_PREC_MIXED = 1, PSL1_PREC_FP32 = 2 };
  *           the fixed point of parareal (Sec. 2.2, Eq. PararealConvergence).
  *  UNIFORM: the uniform L1 scheme on all N fine steps with the whole fine
  *           history (Sec. 2.1, Eq. NumericalSchemeSequential with dt = T/N).
- *  COARSE : U_{n+1} = G_n(U_{0:n}) -- the coarse sweep (parareal step 1).   */
-enum { PSL1_SERIAL_HYBRID = 0, PSL1_SERIAL_UNIFORM = 1, PSL1_SERIAL_COARSE = 2 };
+ *  COARSE : U_{n+1} = G_n(U_{0:n}) -- the coarse sweep (parareal step 1).
+ *  UNIFORM_SOE: the uniform scheme with a fast history (the paper's outlook,
+ *           Conclusion item (i)): the weights b(x) of differences at least
+ *           nloc = 16 steps old are replaced by a sum of exponentials
+ *           sum_i w_i exp(-s_i x) (Gauss-Jacobi and composite Gauss-Legendre
+ *           quadrature of b's Laplace-type integral; 5e-15 relative on
+ *           [16, N] for N <= 8192, 38-80 exponentials), carried as an L x K
+ *           state updated once per step: O((nloc + L) K) work per step
+ *           instead of O(j K).  Captured into a CUDA graph on first use.    */
+enum { PSL1_SERIAL_HYBRID = 0, PSL1_SERIAL_UNIFORM = 1, PSL1_SERIAL_COARSE = 2, PSL1_SERIAL_UNIFORM_SOE = 3 };
 
 /* One problem instance.  Coefficient families (x, y physical coordinates):
  *   D = (d0 + d1/(1+u^2) * X1 + d2*u + d3*sin(pi x)) * X0,
@@ -98,7 +106,24 @@ typedef struct {
     double hi[2];
     double dpar[8];
     double fpar[8];
+    int basis;        /* PSL1_BASIS_SINE (0, default) or PSL1_BASIS_CHEB    */
 } psl1_instance;
+
+/* Spatial scheme of an instance.
+ *  SINE: Galerkin in the sine basis (above); the state is the K = Mx [My]
+ *        modal coefficients.
+ *  CHEB: Chebyshev-Lobatto collocation, the paper's own implementation
+ *        (Sec. 4.1, Eq. NumericalSchemeMainSystem): 1D only, modes[0] = n
+ *        intervals (2 <= n <= 64), nodes x_j = (lo+hi)/2 + (hi-lo)/2
+ *        cos(j pi/n); the state is the K = n - 1 values at the interior
+ *        nodes j = 1..n-1 (u = 0 at j = 0, n); div(D grad u) is Dm diag(D(u))
+ *        Dm restricted to the interior (Dm the scaled first-derivative
+ *        matrix); each step (I - mu N) u = hist + mu f is solved by LU with
+ *        partial pivoting.  qnodes is ignored; handles with collocation
+ *        instances run in PSL1_PREC_FP64 only, and the learned coarse
+ *        correction is not defined for them.  A singular step matrix is
+ *        reported as PSL1_ERR_NOT_SPD.                                       */
+enum { PSL1_BASIS_SINE = 0, PSL1_BASIS_CHEB = 1 };
 
 /* Per-solve statistics filled by the library (device times by CUDA events). */
 typedef struct {
@@ -188,14 +213,60 @@ psl1_status psl1_set_graph(psl1_h h, int on);
  * unchanged; the cheaper early F stages perturb the iterate by about the
  * FP32 step's error (~1e-6 relative), which the later, refined
  * iterations remove, so `above` should stay well above that (1e-4 is used by
- * the benchmark).  Affects MIXED 1D instances only; a no-op for FP64, FP32
- * and 2D.  Rebuilds the parareal graph.  PSL1_ERR_ARG for negative or
+ * the benchmark).  Affects MIXED instances (1D and 2D); a no-op for FP64 and
+ * FP32.  Rebuilds the parareal graph.  PSL1_ERR_ARG for negative or
  * non-finite values.  No counterpart in the paper (an implementation choice:
  * its iteration, Eq. Parareal, uses the same F throughout).                 */
 psl1_status psl1_set_inexact_fine(psl1_h h, double above);
 
 /* Statistics of the last solve.                                             */
 psl1_status psl1_get_stats(psl1_h h, psl1_stats* st);
+
+/* Dense stiffness matrices of the 1D sine-basis instance b (Eq. AForm with
+ * the Gauss quadrature of the step), for `units` sets of nodal diffusivities:
+ *   A_u[k][l] = sum_q w_q D_u(x_q) phi_{k+1}'(x_q) phi_{l+1}'(x_q),
+ * D: units x Q doubles at the Q nodes in ascending order (host); A: units x
+ * K x K floats, row-major (host).  The solver never forms this matrix (it
+ * applies the Toeplitz+Hankel form, O(QK) per step); this entry point
+ * measures that choice against the dense contraction:
+ *  PSL1_ASSEMBLE_TENSOR : A = Phi'^T diag(w D) Phi' as a GEMM on the tensor
+ *      cores (tcgen05.mma kind::f16, BF16 operands, FP32 accumulation in
+ *      tensor memory; one CTA per unit and 128-row block; K <= 256).  Each
+ *      entry is within 2^-7 sqrt(A_kk A_ll) of the exact sum (BF16 rounding
+ *      of both operands).
+ *  PSL1_ASSEMBLE_MOMENTS: the 2K+1 moments g_s = sum_q w_q D_q cos(s pi
+ *      th_q) in FP32, A_kl = cA k l (g_|k-l| + g_{k+l}).
+ * ms (may be NULL) receives the device time of the assembly kernel alone.
+ * Table set-up and copies are outside that time.  PSL1_ERR_TIMEOUT if a
+ * bounded wait of the tensor-core kernel gave up.  No counterpart in the
+ * paper (its implementation is collocation; the moment form is this
+ * library's).                                                              */
+enum { PSL1_ASSEMBLE_TENSOR = 0, PSL1_ASSEMBLE_MOMENTS = 1 };
+psl1_status psl1_assemble(psl1_h h, int b, int method, int units, const double* D, float* A, float* ms);
+
+/* Autotuning of the F stage for this handle's batch (no counterpart in the
+ * paper).  Tuned by timing one F stage (iteration 0, every slice) per
+ * candidate on the handle's own instances and u0 (set it first):
+ *  - PSL1_PREC_MIXED: the relative residual of the FP32 inner CG of the
+ *    refined step, per bucket of instances with K in (2^(j-1), 2^j]
+ *    (candidates 1e-7 (default), 1e-5, 3e-4: a looser inner solve means
+ *    fewer CG iterations and more double-float refinement sweeps); a
+ *    candidate is kept only if its slice-end states agree with the
+ *    default's to 1e-10 relative;
+ *  - every precision: the persistent F stage's CTAs, one or two per SM.
+ * cache_path (may be NULL): a file of JSON lines {"key": ..., "value": ...}
+ * keyed by device name, precision, dimension and bucket (or unit count);
+ * cached choices are applied without timing, new ones are appended.
+ * from_cache (may be NULL) receives 1 if every choice came from the cache.
+ * The parareal graph is rebuilt on the next graph-mode solve.              */
+psl1_status psl1_autotune(psl1_h h, const char* cache_path, int* from_cache);
+/* The tuned inner tolerance of instance b and the F stage's CTA count.      */
+psl1_status psl1_get_tuning(psl1_h h, int b, float* inner_rtol, int* fstage_ctas);
+
+/* Exponents s and weights w (cap entries each, may be NULL) of the fast/* Exponents s and weights w (cap entries each, may be NULL) of the fast/* Exponents s and weights w (cap entries each, may be NULL) of the fast
+ * history of instance b: b(x) ~ sum_i w_i exp(-s_i x) for 16 <= x <= N_b;
+ * len receives their number (0 for alpha = 1, which has no history).       */
+psl1_status psl1_get_soe(psl1_h h, int b, double* s, double* w, int cap, int* len);
 
 /* ---- single pieces of the path, for checks at full size ----------------- */
 /* One linearised step of instance b (Eq. NumericalSchemeSequential form):
@@ -217,18 +288,25 @@ psl1_status psl1_fine_slice(psl1_h h, int b, int n, const double* U, double* V);
  * real-time loop whose device memory was all planned before it started,
  * or code running under a memory manager that forbids new allocations --
  * after creating the handle where allocation was still allowed.
- * Scratch (the fine-history ring of m K_b doubles plus, for PSL1_PREC_FP64 or
- * a factor too large for shared memory, the factor workspace) comes from one
- * fixed 4 MiB device array compiled into the library, which every device that
- * loads the library keeps until the process exits.  Instances whose scratch
- * exceeds 4 MiB are rejected with PSL1_ERR_ARG (the message gives the need).
- * The first call on a device looks up that array's device address (with the
- * device current), so make the first call before any stream capture.  All
- * calls share the array and it keeps the last call's contents; every element
- * is written before it is read, so nothing needs clearing, but calls that
- * overlap on the GPU (for instance from two handles on different streams)
- * race.  Ordered on the handle's stream; returns after the kernel finished,
- * with device-side failures reported as in psl1_fine_slice.                */
+ * Scratch comes from one fixed 4 MiB device array compiled into the library
+ * (512 Ki doubles), which every device that loads the library keeps until the
+ * process exits.  It holds, each region starting on a 256-byte boundary:
+ *   the fine-history ring, m K_b doubles;
+ *   PSL1_PREC_FP64 1D: the blocked Cholesky factor, nb (nb+1)/2 32x32 blocks
+ *     (nb = ceil(K_b/32)); 2D: the working arrays that do not fit in shared
+ *     memory (none for small mode counts; the node arrays at 64 x 64 modes);
+ *   PSL1_PREC_MIXED / FP32: the coarse differences U_i - U_{i-1}, (n+1) K_b
+ *     entries of 8 bytes.
+ * An instance whose scratch exceeds the array is rejected with PSL1_ERR_ARG
+ * (the message gives the need).  psl1_create looks up the array's device
+ * address with the handle's device current (this loads the library's kernel
+ * module there, which is when the array is placed), so this call needs no
+ * set-up of its own; a handle is invalid after cudaDeviceReset, the address
+ * with it.  All calls share the array and it keeps the last call's contents;
+ * every element is written before it is read, so nothing needs clearing, but
+ * calls that overlap on the GPU (for instance from two handles on different
+ * streams) race.  Ordered on the handle's stream; returns after the kernel
+ * finished, with device-side failures reported as in psl1_fine_slice.       */
 psl1_status psl1_fine_slice_noalloc(psl1_h h, int b, int n, const double* d_U, double* d_V);
 
 /* Coarse propagator G_n of instance b on U_0..U_n (host); out: K_b doubles. */

@@ -13,6 +13,8 @@
 
 #include "psl1.h"
 #include "psl1_kernels.h"
+#include "psl1_soe.h"
+#include "psl1_tc.h"
 
 using namespace psl1;
 
@@ -24,6 +26,16 @@ struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
 };
+
+// w_q D_q (FP32, padded to Qpad) from nodal D (FP64) and the unfolded weights
+__global__ void k_tc_weights(const double* D, const float* w, int units, int Q, int Qpad, float* wD)
+{
+    const long long n = (long long)units * Qpad;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(e / Qpad), q = (int)(e % Qpad);
+        wD[e] = q < Q ? (float)((double)w[q] * D[(size_t)u * Q + q]) : 0.f;
+    }
+}
 
 }  // namespace
 
@@ -51,10 +63,18 @@ struct psl1_problem {
     int nunits = 0;
     DevStatus* d_status = nullptr;
     double* d_flops = nullptr;   // algorithmic FLOP accumulators: F stage, coarse, serial, pieces
+    double* d_noalloc = nullptr;  // device address of the library's fixed scratch array (not owned)
+    double* d_cheb = nullptr;     // collocation pool: per instance nodes, sines and derivative matrix
+    int fgrid = 0;                // F-stage CTAs chosen by psl1_autotune (0: one per slot)
     // uniform solver pools (lazy)
     double *d_Wcur = nullptr, *d_dW = nullptr, *d_part = nullptr;
     int uni_chunk = 32, uni_maxchunks = 0;   // history rows per CTA of k_uni_hist (autotuned)
     cudaGraphExec_t uni_graph = nullptr;   // the uniform solver's N-step launch sequence
+    // fast (sum-of-exponentials) uniform history (lazy)
+    double *d_soe = nullptr, *d_Y = nullptr;
+    long long sumY = 0;
+    cudaGraphExec_t soe_graph = nullptr;
+    std::vector<std::vector<double>> soe_s, soe_w;
     // graph-mode parareal (device-driven while loop)
     bool graph_mode = false;
     cudaGraphExec_t par_graph = nullptr;
@@ -165,6 +185,7 @@ void psl1_destroy(psl1_h h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->uni_graph) cudaGraphExecDestroy(h->uni_graph);
+    if (h->soe_graph) cudaGraphExecDestroy(h->soe_graph);
     if (h->par_graph) cudaGraphExecDestroy(h->par_graph);
     for (void* p : h->allocs) cudaFree(p);
     for (auto& e : h->ev)
@@ -188,9 +209,57 @@ static void family_copies(InstDev& I)
     I.f_df = (I.fpar[4] == 0.0 && I.fpar[5] == 0.0) ? 1 : 0;
 }
 
+// Chebyshev-Lobatto collocation data of n intervals on [a, b] (Sec. 4.1), appended
+// to pool: nodes x_j = (a+b)/2 + (b-a)/2 cos(j pi/n), sin(pi x_j), sin(2 pi x_j), and
+// the first-derivative matrix scaled by 2/(b-a) with the entries the paper gives,
+//   D_ij = (c_i/c_j) (-1)^{i+j} / (xi_i - xi_j),  c_0 = c_n = 2, else 1,
+//   D_00 = (2n^2+1)/6,  D_nn = -(2n^2+1)/6,  D_jj = -xi_j / (2 (1 - xi_j^2)),
+// where xi_i - xi_j = -2 sin((i+j) pi/2n) sin((i-j) pi/2n) and 1 - xi_j^2 =
+// sin^2(j pi/n) are taken in these trigonometric forms (no cancellation).
+static void cheb_tables(int n, double a, double b, std::vector<double>& pool)
+{
+    const int Q = n + 1;
+    const size_t o = pool.size();
+    pool.resize(o + 3 * (size_t)Q + (size_t)Q * Q);
+    double* x = pool.data() + o;
+    double* s1 = x + Q;
+    double* s2 = s1 + Q;
+    double* D = s2 + Q;
+    const double h = M_PI / n, sc = 2.0 / (b - a);
+    for (int j = 0; j < Q; ++j) {
+        x[j] = 0.5 * (a + b) + 0.5 * (b - a) * std::cos(j * h);
+        s1[j] = std::sin(M_PI * x[j]);
+        s2[j] = std::sin(2.0 * M_PI * x[j]);
+    }
+    for (int i = 0; i < Q; ++i)
+        for (int j = 0; j < Q; ++j) {
+            double v;
+            if (i == j) {
+                if (i == 0)
+                    v = (2.0 * n * n + 1.0) / 6.0;
+                else if (i == n)
+                    v = -(2.0 * n * n + 1.0) / 6.0;
+                else {
+                    const double sn = std::sin(i * h);
+                    v = -std::cos(i * h) / (2.0 * sn * sn);
+                }
+            } else {
+                const double ci = (i == 0 || i == n) ? 2.0 : 1.0, cj = (j == 0 || j == n) ? 2.0 : 1.0;
+                const double diff = -2.0 * std::sin(0.5 * (i + j) * h) * std::sin(0.5 * (i - j) * h);
+                v = (ci / cj) * (((i + j) & 1) ? -1.0 : 1.0) / diff;
+            }
+            D[(size_t)i * Q + j] = sc * v;
+        }
+}
+
 static psl1_status validate(const psl1_instance& d, int P, int b)
 {
     if (d.dim != 1 && d.dim != 2) return fail(nullptr, PSL1_ERR_ARG, "instance %d: dim must be 1 or 2", b);
+    if (d.basis != PSL1_BASIS_SINE && d.basis != PSL1_BASIS_CHEB)
+        return fail(nullptr, PSL1_ERR_ARG, "instance %d: unknown basis %d", b, d.basis);
+    if (d.basis == PSL1_BASIS_CHEB && (d.dim != 1 || d.modes[0] < 2 || d.modes[0] > CHEB_NMAX))
+        return fail(nullptr, PSL1_ERR_ARG, "instance %d: collocation needs dim 1 and 2 <= intervals <= %d", b,
+                    CHEB_NMAX);
     const int mmax = d.dim == 1 ? KMAX_1D : MMAX_2D;
     for (int ax = 0; ax < d.dim; ++ax) {
         int M = d.modes[ax];
@@ -223,6 +292,9 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     if (precision != PSL1_PREC_FP64 && precision != PSL1_PREC_MIXED && precision != PSL1_PREC_FP32)
         return fail(nullptr, PSL1_ERR_ARG, "unknown precision %d", precision);
     for (int b = 0; b < batch; ++b) TRY(validate(in[b], P, b));
+    for (int b = 0; b < batch; ++b)
+        if (in[b].basis == PSL1_BASIS_CHEB && precision != PSL1_PREC_FP64)
+            return fail(nullptr, PSL1_ERR_ARG, "instance %d: the collocation scheme runs in PSL1_PREC_FP64", b);
     for (int b = 1; b < batch; ++b)
         if (in[b].dim != in[0].dim)
             return fail(nullptr, PSL1_ERR_ARG, "instance %d: all instances of a handle must have the same dim", b);
@@ -324,14 +396,18 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     };
     h->inst.resize(batch);
     long long nT2 = 0, nN2 = 0, ntab2 = 0;
+    std::vector<double> cheb_pool;
+    int Kc = 0;
     for (int b = 0; b < batch; ++b) {
         const psl1_instance& d = in[b];
         InstDev& I = h->inst[b];
         memset(&I, 0, sizeof I);
         I.dim = d.dim;
+        I.basis = d.basis;
+        I.inner_rtol = INNER_RTOL_DEFAULT;
         I.Mx = d.modes[0];
         I.My = d.dim == 2 ? d.modes[1] : 1;
-        I.K = I.Mx * I.My;
+        I.K = I.basis == PSL1_BASIS_CHEB ? I.Mx - 1 : I.Mx * I.My;
         I.nb = (I.K + TILE - 1) / TILE;
         I.Kp = I.nb * TILE;
         I.Q = d.qnodes[0] ? d.qnodes[0] : 2 * I.Mx;
@@ -365,6 +441,11 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         } else {
             I.tabY = I.tab;
         }
+        if (I.basis == PSL1_BASIS_CHEB) {   // nodes, sin(pi x), sin(2 pi x), derivative matrix
+            I.oC = (long long)cheb_pool.size();
+            cheb_tables(I.Mx, I.lo0, I.hi0, cheb_pool);
+            Kc = std::max(Kc, I.K);
+        }
         I.Nb = std::max(std::max(I.N, P), I.m) + 1;
         I.oK = h->sumK;
         h->sumK += I.K;
@@ -393,7 +474,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         lay2 = make_layout2d(precision, h->Kmax, nT2, nN2, ntab2, max_smem - 1024);
         lay.total = lay2.smem;
     } else {
-        lay = make_layout(precision, h->Kmax, h->Kpmax, h->Qhmax);
+        lay = make_layout(precision, h->Kmax, h->Kpmax, h->Qhmax, Kc);
     }
     if (lay.total > max_smem - 1024) {
         g_create_error = "instance too large for the shared-memory layout";
@@ -417,7 +498,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     CTRY(dalloc(h, &h->d_counter, 1));
     CTRY(dalloc(h, &h->d_status, 1));
     CTRY(dalloc(h, &h->d_flops, 4));
-    // per-slot factor workspace: FP64 factor, or the FP32 factor when it does not fit in shared memory
+    if (!cheb_pool.empty()) CTRY(dalloc(h, &h->d_cheb, cheb_pool.size()));
+    // per-slot workspace: the FP64 1D factor, or the 2D working arrays that do not fit in shared memory
     long long work_stride = two_d ? std::max(1LL, (lay2.gbytes + 255) / 256 * 32)   // 256-byte aligned slots
                             : precision == PSL1_PREC_FP64 ? bp_elems(nbmax, TILE)
                             : 1;
@@ -475,6 +557,9 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     CTRY(cu(cudaMemcpyAsync(h->d_units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice,
                             h->stream), "copy units"));
     CTRY(cu(cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream), "status"));
+    if (!cheb_pool.empty())
+        CTRY(cu(cudaMemcpyAsync(h->d_cheb, cheb_pool.data(), sizeof(double) * cheb_pool.size(),
+                                cudaMemcpyHostToDevice, h->stream), "copy collocation tables"));
     for (auto& j : jobs) CTRY(cu(launch_tables(j, h->stream), "table kernels"));
     CTRY(cu(launch_weights(h->d_inst, batch, h->d_bp, h->d_bpd, h->stream), "weight kernel"));
     // constants computed on the device (mu, muT, ...) are needed on the host copy too
@@ -482,6 +567,9 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
             "read constants"));
     CTRY(cu(cudaStreamSynchronize(h->stream), "set-up"));
     for (auto& ev : h->ev) CTRY(cu(cudaEventCreate(&ev), "events"));
+    // the allocation-free fine propagator's fixed array: its device address on this
+    // device, looked up here so that psl1_fine_slice_noalloc needs no set-up
+    CTRY(cu(noalloc_scratch_address(&h->d_noalloc), "address of the fixed scratch array"));
 
     PathArgs& a = h->pa;
     a.inst = h->d_inst;
@@ -509,6 +597,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.L2 = lay2;
     a.incr = h->d_incr;
     a.loose_above = 0.0;
+    a.cheb = h->d_cheb;
     h->iters.assign(batch, 0);
     h->errlog.assign(batch, {});
     h->d_Ucur = h->d_Ua;
@@ -637,6 +726,70 @@ static cudaError_t enqueue_uniform(psl1_problem* h)
     return e;
 }
 
+// The fast uniform history: the exponentials of every instance (host, psl1_soe.cu),
+// their device pool exp(-s), exp(-s nloc), w, and the L x K state of each instance.
+static psl1_status ensure_soe_pools(psl1_problem* h)
+{
+    if (h->d_Y) return PSL1_OK;
+    TRY(ensure_uniform_pools(h));
+    std::vector<double> pool;
+    h->soe_s.assign(h->B, {});
+    h->soe_w.assign(h->B, {});
+    long long oY = 0;
+    for (int b = 0; b < h->B; ++b) {
+        InstDev& I = h->inst[b];
+        double sv[SOE_MAXL], wv[SOE_MAXL];
+        const int L = soe_nodes(I.alpha, SOE_NLOC, I.N, SOE_EPS, SOE_MAXL, sv, wv);
+        if (L < 0) return fail(h, PSL1_ERR_ARG, "instance %d: no fast-history exponentials", b);
+        I.soeL = L;
+        I.oS = (long long)pool.size();
+        I.oY = oY;
+        for (int i = 0; i < L; ++i) pool.push_back(std::exp(-sv[i]));
+        for (int i = 0; i < L; ++i) pool.push_back(std::exp(-sv[i] * SOE_NLOC));
+        for (int i = 0; i < L; ++i) pool.push_back(wv[i]);
+        h->soe_s[b].assign(sv, sv + L);
+        h->soe_w[b].assign(wv, wv + L);
+        oY += (long long)L * I.K;
+    }
+    h->sumY = oY;
+    TRY(dalloc(h, &h->d_soe, std::max<size_t>(pool.size(), 1)));
+    TRY(dalloc(h, &h->d_Y, (size_t)std::max(oY, 1LL)));
+    CU(h, cudaMemcpyAsync(h->d_soe, pool.data(), sizeof(double) * pool.size(), cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(InstDev) * h->B, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    return PSL1_OK;
+}
+
+// The fast uniform solver's launches: initial state, a cleared exponential
+// state, then one fused history + step launch per fine step.
+static cudaError_t enqueue_uniform_soe(psl1_problem* h)
+{
+    cudaError_t e = launch_uni_init(h->pa, h->B, h->d_u0, h->d_Wcur, h->d_Us, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->d_Y, 0, sizeof(double) * std::max(h->sumY, 1LL), h->stream);
+    for (int j = 0; j < h->Nmax && e == cudaSuccess; ++j)
+        e = launch_uni_soe_step(h->pa, h->B, h->d_Wcur, h->d_dW, h->d_Us, j, h->d_soe, h->d_Y, SOE_NLOC,
+                                h->stream);
+    return e;
+}
+
+// Capture an N-step launch sequence into a graph (once per handle).
+static psl1_status capture(psl1_problem* h, cudaGraphExec_t* out, cudaError_t (*enq)(psl1_problem*), const char* what)
+{
+    cudaGraph_t g = nullptr;
+    CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enq(h);
+    cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return fail(h, PSL1_ERR_CUDA, "%s graph: %s", what, cudaGetErrorString(e));
+    }
+    return PSL1_OK;
+}
+
 psl1_status psl1_solve_serial(psl1_h h, int kind)
 {
     if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
@@ -666,20 +819,22 @@ psl1_status psl1_solve_serial(psl1_h h, int kind)
         if (!h->uni_graph) {
             TRY(tune_uniform_chunk(h));
             CU(h, cudaEventRecord(h->ev[0], h->stream));   // the timed solve starts after the tuning
-            cudaGraph_t g = nullptr;
-            CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = enqueue_uniform(h);
-            cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
-            if (e == cudaSuccess) e = ee;
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->uni_graph, g, 0);
-            if (g) cudaGraphDestroy(g);
-            if (e != cudaSuccess) {
-                h->uni_graph = nullptr;
-                return fail(h, PSL1_ERR_CUDA, "uniform solver graph: %s", cudaGetErrorString(e));
-            }
+            TRY(capture(h, &h->uni_graph, enqueue_uniform, "uniform solver"));
         }
         CU(h, cudaGraphLaunch(h->uni_graph, h->stream));
         h->stats.kernel_launches = 2 * h->Nmax;   // init + (N - 1) history + N step kernels
+        for (int b = 0; b < h->B; ++b) {
+            h->stats.fine_steps += h->inst[b].N;
+            h->stats.fine_step_modes += (double)h->inst[b].N * h->inst[b].K;
+        }
+    } else if (kind == PSL1_SERIAL_UNIFORM_SOE) {
+        TRY(ensure_soe_pools(h));
+        if (!h->soe_graph) {
+            TRY(capture(h, &h->soe_graph, enqueue_uniform_soe, "fast uniform solver"));
+            CU(h, cudaEventRecord(h->ev[0], h->stream));
+        }
+        CU(h, cudaGraphLaunch(h->soe_graph, h->stream));
+        h->stats.kernel_launches = 1 + h->Nmax;   // init + N fused history/step kernels
         for (int b = 0; b < h->B; ++b) {
             h->stats.fine_steps += h->inst[b].N;
             h->stats.fine_step_modes += (double)h->inst[b].N * h->inst[b].K;
@@ -742,6 +897,13 @@ psl1_status psl1_set_graph(psl1_h h, int on)
 // The graph-mode iteration: a while node whose body is
 //   F stage (U^k -> F_old), correction sweep (U^k -> U^{k+1}, e_k), U^k <- U^{k+1},
 //   update (log e_k, retire converged instances, k += 1, loop condition).
+// CTAs of the persistent F stage: the tuned count, at most one per workspace slot
+static int fstage_grid(const psl1_problem* h)
+{
+    const int g = h->fgrid > 0 ? std::min(h->fgrid, h->pa.nslots) : h->pa.nslots;
+    return std::min(h->nunits, g);
+}
+
 static psl1_status build_parareal_graph(psl1_problem* h)
 {
     if (!h->d_iters) {
@@ -767,7 +929,7 @@ static psl1_status build_parareal_graph(psl1_problem* h)
         cudaGraph_t body = np.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const int grid = std::min(h->nunits, h->pa.nslots);
+            const int grid = fstage_grid(h);
             cudaError_t q = launch_fstage(h->pa, h->d_Ua, h->d_Fv, h->d_units, h->nunits, h->d_counter, h->d_nfirst,
                                           h->d_active, grid, h->stream);
             if (q == cudaSuccess)
@@ -873,7 +1035,7 @@ psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_o
         CU(h, cudaMemcpyAsync(h->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, h->stream));
         CU(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
         CU(h, cudaEventRecord(h->ev[0], h->stream));
-        int grid = std::min(h->nunits, h->pa.nslots);
+        int grid = fstage_grid(h);
         CU(h, launch_fstage(h->pa, Uk, h->d_Fv, h->d_units, h->nunits, h->d_counter, h->d_nfirst, h->d_active,
                             grid, h->stream));
         CU(h, cudaEventRecord(h->ev[1], h->stream));
@@ -953,6 +1115,196 @@ psl1_status psl1_get_iterate(psl1_h h, int k, double* out)
     return PSL1_OK;
 }
 
+// ---------------------------------------------------------------- autotuning
+// Candidates of the refined mixed step's FP32 inner CG tolerance: a looser
+// inner solve takes fewer CG iterations and more refinement sweeps (each with
+// a double-float residual); the best balance depends on K.
+static const float kInnerRtol[] = {1e-7f, 1e-5f, 3e-4f};
+
+static std::string tune_device_name()
+{
+    int d = 0;
+    cudaDeviceProp pr{};
+    if (cudaGetDevice(&d) != cudaSuccess || cudaGetDeviceProperties(&pr, d) != cudaSuccess) return "unknown";
+    return pr.name;
+}
+
+// cache file: one JSON object per line, {"key": "...", "value": <number>}
+static std::map<std::string, double> tune_read(const char* path)
+{
+    std::map<std::string, double> m;
+    if (!path) return m;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return m;
+    char line[1024];
+    while (std::fgets(line, sizeof line, f)) {
+        const char* k = std::strstr(line, "\"key\": \"");
+        const char* v = std::strstr(line, "\"value\": ");
+        if (!k || !v) continue;
+        k += 8;   // past "key": "
+        const char* e = std::strchr(k, '"');
+        if (!e) continue;
+        m[std::string(k, e - k)] = std::strtod(v + 9, nullptr);
+    }
+    std::fclose(f);
+    return m;
+}
+
+// one F stage (all slices, iteration 0) of the instances in `active`, timed on
+// the second of two launches; optionally the slice-end states
+static psl1_status fstage_trial(psl1_problem* h, const std::vector<int>& active, float* ms, std::vector<double>* Fv)
+{
+    std::vector<int> nf(h->B, 0);
+    CU(h, cudaMemcpyAsync(h->d_nfirst, nf.data(), sizeof(int) * h->B, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->d_active, active.data(), sizeof(int) * h->B, cudaMemcpyHostToDevice, h->stream));
+    for (int rep = 0; rep < 2; ++rep) {
+        CU(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
+        if (rep == 1) CU(h, cudaEventRecord(h->ev[2], h->stream));
+        CU(h, launch_fstage(h->pa, h->d_Ua, h->d_Fv, h->d_units, h->nunits, h->d_counter, h->d_nfirst, h->d_active,
+                            fstage_grid(h), h->stream));
+        if (rep == 1) CU(h, cudaEventRecord(h->ev[3], h->stream));
+    }
+    TRY(check_device_status(h));
+    CU(h, cudaEventElapsedTime(ms, h->ev[2], h->ev[3]));
+    if (Fv) {
+        Fv->resize(h->sumPK);
+        CU(h, cudaMemcpy(Fv->data(), h->d_Fv, sizeof(double) * h->sumPK, cudaMemcpyDeviceToHost));
+    }
+    return PSL1_OK;
+}
+
+psl1_status psl1_autotune(psl1_h h, const char* cache_path, int* from_cache)
+{
+    if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
+    if (!h->u0_set) return fail(h, PSL1_ERR_STATE, "set u0 before tuning");
+    const std::string dev = tune_device_name();
+    const char* prec = h->prec == PSL1_PREC_FP64 ? "fp64" : h->prec == PSL1_PREC_MIXED ? "mixed" : "fp32";
+    const char* dim = h->pa.dim2 ? "2d" : "1d";
+    std::map<std::string, double> cache = tune_read(cache_path);
+    std::vector<std::pair<std::string, double>> fresh;
+    int hits = 0, misses = 0;
+    const double loose = h->pa.loose_above;
+    h->pa.loose_above = 0.0;   // tune the refined step
+    TRY(reset_status(h));
+    CU(h, launch_coarse_sweep(h->pa, h->B, h->d_u0, nullptr, h->d_Ua, nullptr, h->d_Gold, 1, h->d_nfirst,
+                              h->d_active, h->d_incr, h->stream));   // U^0, the states every trial starts from
+    psl1_status st = PSL1_OK;
+    // (1) inner tolerance per K bucket (powers of two), refined mixed sine-basis step
+    if (h->prec == PSL1_PREC_MIXED) {
+        std::map<int, std::vector<int>> buckets;
+        for (int b = 0; b < h->B; ++b) {
+            if (h->inst[b].basis != PSL1_BASIS_SINE) continue;
+            int kb = 1;
+            while (kb < h->inst[b].K) kb <<= 1;
+            buckets[kb].push_back(b);
+        }
+        for (auto& bk : buckets) {
+            char key[256];
+            std::snprintf(key, sizeof key, "%s|%s|%s|inner_rtol|K<=%d", dev.c_str(), prec, dim, bk.first);
+            auto set_rtol = [&](float r) -> psl1_status {
+                for (int b : bk.second) h->inst[b].inner_rtol = r;
+                CU(h, cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(InstDev) * h->B, cudaMemcpyHostToDevice,
+                                      h->stream));
+                return PSL1_OK;
+            };
+            auto it = cache.find(key);
+            if (it != cache.end()) {
+                if ((st = set_rtol((float)it->second)) != PSL1_OK) break;
+                ++hits;
+                continue;
+            }
+            ++misses;
+            std::vector<int> act(h->B, 0);
+            for (int b : bk.second) act[b] = 1;
+            std::vector<double> ref, F;
+            float best_ms = 0.f, ms = 0.f;
+            float best = kInnerRtol[0];
+            if ((st = set_rtol(best)) != PSL1_OK || (st = fstage_trial(h, act, &best_ms, &ref)) != PSL1_OK) break;
+            for (size_t c = 1; c < sizeof kInnerRtol / sizeof kInnerRtol[0] && st == PSL1_OK; ++c) {
+                if ((st = set_rtol(kInnerRtol[c])) != PSL1_OK || (st = fstage_trial(h, act, &ms, &F)) != PSL1_OK) break;
+                // keep a candidate only if its slice-end states agree with the default's to 1e-10
+                double num = 0.0, den = 0.0;
+                for (int b : bk.second) {
+                    const InstDev& I = h->inst[b];
+                    for (long long e = I.oPK; e < I.oPK + (long long)h->P * I.K; ++e) {
+                        num = std::max(num, std::fabs(F[e] - ref[e]));
+                        den = std::max(den, std::fabs(ref[e]));
+                    }
+                }
+                if (num <= 1e-10 * den && ms < best_ms) {
+                    best_ms = ms;
+                    best = kInnerRtol[c];
+                }
+            }
+            if (st != PSL1_OK || (st = set_rtol(best)) != PSL1_OK) break;
+            fresh.push_back({key, (double)best});
+        }
+    }
+    // (2) CTAs of the persistent F stage: one or two per SM
+    if (st == PSL1_OK) {
+        char key[256];
+        std::snprintf(key, sizeof key, "%s|%s|%s|fstage_grid|units=%d|slots=%d", dev.c_str(), prec, dim, h->nunits,
+                      h->pa.nslots);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            h->fgrid = (int)it->second;
+            ++hits;
+        } else {
+            ++misses;
+            std::vector<int> act(h->B, 1);
+            int best = 0;
+            float best_ms = 0.f;
+            for (int g : {h->nsm, 2 * h->nsm}) {
+                if (g > h->pa.nslots) continue;
+                h->fgrid = g;
+                float ms = 0.f;
+                if ((st = fstage_trial(h, act, &ms, nullptr)) != PSL1_OK) break;
+                if (best == 0 || ms < best_ms) {
+                    best = g;
+                    best_ms = ms;
+                }
+            }
+            h->fgrid = best;
+            if (st == PSL1_OK) fresh.push_back({key, (double)best});
+        }
+    }
+    h->pa.loose_above = loose;
+    if (h->par_graph) {   // the graph holds the launch configuration
+        cudaGraphExecDestroy(h->par_graph);
+        h->par_graph = nullptr;
+    }
+    if (st != PSL1_OK) return st;
+    if (cache_path && !fresh.empty()) {
+        FILE* f = std::fopen(cache_path, "a");
+        if (!f) return fail(h, PSL1_ERR_ARG, "cannot write the tuning cache %s", cache_path);
+        for (auto& kv : fresh) std::fprintf(f, "{\"key\": \"%s\", \"value\": %.9g}\n", kv.first.c_str(), kv.second);
+        std::fclose(f);
+    }
+    if (from_cache) *from_cache = (misses == 0 && hits > 0) ? 1 : 0;
+    return PSL1_OK;
+}
+
+psl1_status psl1_get_tuning(psl1_h h, int b, float* inner_rtol, int* fstage_ctas)
+{
+    if (!h || b < 0 || b >= h->B) return fail(h, PSL1_ERR_ARG, "bad argument");
+    if (inner_rtol) *inner_rtol = h->inst[b].inner_rtol;
+    if (fstage_ctas) *fstage_ctas = fstage_grid(h);
+    return PSL1_OK;
+}
+
+psl1_status psl1_get_soe(psl1_h h, int b, double* s, double* w, int cap, int* len)
+{
+    if (!h || b < 0 || b >= h->B || !len || cap < 0) return fail(h, PSL1_ERR_ARG, "bad argument");
+    if (!h->d_Y) TRY(ensure_soe_pools(h));
+    const int L = (int)h->soe_s[b].size();
+    *len = L;
+    for (int i = 0; i < L && i < cap; ++i) {
+        if (s) s[i] = h->soe_s[b][i];
+        if (w) w[i] = h->soe_w[b][i];
+    }
+    return PSL1_OK;
+}
+
 psl1_status psl1_get_stats(psl1_h h, psl1_stats* st)
 {
     if (!h || !st) return fail(h, PSL1_ERR_ARG, "NULL argument");
@@ -976,6 +1328,58 @@ struct TmpDev {
         return (double*)q;
     }
 };
+
+// ---------------------------------------------------------------- dense assembly (measurement of the choice)
+psl1_status psl1_assemble(psl1_h h, int b, int method, int units, const double* D, float* A, float* ms)
+{
+    if (!h || !D || !A || b < 0 || b >= h->B || units < 1) return fail(h, PSL1_ERR_ARG, "bad argument");
+    const InstDev& I = h->inst[b];
+    if (I.dim != 1 || I.basis != PSL1_BASIS_SINE)
+        return fail(h, PSL1_ERR_ARG, "dense assembly is defined for 1D sine-basis instances");
+    if (method != PSL1_ASSEMBLE_TENSOR && method != PSL1_ASSEMBLE_MOMENTS)
+        return fail(h, PSL1_ERR_ARG, "unknown assembly method %d", method);
+    const int K = I.K, Q = I.Q, Qh = I.Qh;
+    if (method == PSL1_ASSEMBLE_TENSOR && K > TC_KMAX)
+        return fail(h, PSL1_ERR_ARG, "tensor-core assembly needs K <= %d (K = %d)", TC_KMAX, K);
+    const int Kpad = (K + 127) / 128 * 128, Npad = (K + 15) / 16 * 16, Qpad = (Q + 63) / 64 * 64;
+    const TabDev& T = h->tabs[I.tab];
+    TmpDev t{h};
+    double* dD = t.get((size_t)units * Q);
+    double* tphi = t.get(((size_t)Kpad * Qpad + 3) / 4);               // BF16 table
+    double* tcos = t.get(((size_t)Q * (2 * K + 1) + 1) / 2);           // FP32 cosines
+    double* tw = t.get((Q + 1) / 2);                                   // FP32 weights
+    double* twD = t.get(((size_t)units * Qpad + 1) / 2);                // FP32 w D
+    double* tA = t.get(((size_t)units * K * K + 1) / 2);                // FP32 result
+    double* tst = t.get(1);
+    if (!dD || !tphi || !tcos || !tw || !twD || !tA || !tst) return fail(h, PSL1_ERR_NOMEM, "scratch allocation failed");
+    auto* phiT = reinterpret_cast<__nv_bfloat16*>(tphi);
+    float *cosT = reinterpret_cast<float*>(tcos), *w = reinterpret_cast<float*>(tw);
+    float *wD = reinterpret_cast<float*>(twD), *dA = reinterpret_cast<float*>(tA);
+    int* st = reinterpret_cast<int*>(tst);
+    CU(h, cudaMemsetAsync(st, 0, sizeof(int), h->stream));
+    CU(h, cudaMemcpyAsync(dD, D, sizeof(double) * units * Q, cudaMemcpyHostToDevice, h->stream));
+    CU(h, launch_tc_tables(h->d_tp + T.oDt, h->d_tp + T.oC, h->d_tp + T.oWq, K, Qh, Kpad, Qpad, phiT, cosT, w,
+                           h->stream));
+    k_tc_weights<<<256, 256, 0, h->stream>>>(dD, w, units, Q, Qpad, wD);
+    CU(h, cudaGetLastError());
+    CU(h, cudaEventRecord(h->ev[2], h->stream));
+    if (method == PSL1_ASSEMBLE_TENSOR)
+        CU(h, launch_assemble_tc(phiT, wD, units, K, Npad, Kpad, Qpad, dA, st, h->stream));
+    else
+        CU(h, launch_assemble_th(cosT, wD, units, K, Qpad, Q, (float)I.cA, dA, h->stream));
+    CU(h, cudaEventRecord(h->ev[3], h->stream));
+    int hst = 0;
+    CU(h, cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaMemcpyAsync(A, dA, sizeof(float) * units * K * K, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    if (hst) return fail(h, PSL1_ERR_TIMEOUT, "tensor-core assembly: a bounded wait on the MMA barrier gave up");
+    if (ms) {
+        float e = 0.f;
+        CU(h, cudaEventElapsedTime(&e, h->ev[2], h->ev[3]));
+        *ms = e;
+    }
+    return PSL1_OK;
+}
 
 psl1_status psl1_step(psl1_h h, int b, const double* c, double te, double mu, const double* hist, double* out)
 {
@@ -1011,18 +1415,21 @@ psl1_status psl1_fine_slice_noalloc(psl1_h h, int b, int n, const double* d_U, d
     if (!h || !d_U || !d_V || b < 0 || b >= h->B || n < 0 || n >= h->P)
         return fail(h, PSL1_ERR_ARG, "bad argument");
     const InstDev& I = h->inst[b];
+    // scratch: the fine-history ring, then the FP64 1D factor or the 2D working arrays
+    // outside shared memory, then the coarse differences of the FP32-pipe paths
     long long ring = (long long)I.m * I.K;
-    long long work = h->pa.dim2 ? h->pa.work_stride   // 2D working arrays outside shared memory
+    long long work = h->pa.dim2 ? h->pa.work_stride
                      : h->prec == PSL1_PREC_FP64 ? bp_elems(I.nb, TILE)
                      : 0;
-    long long dud = h->prec == PSL1_PREC_FP64 ? 0 : (long long)(n + 1) * I.K;   // coarse differences
-    if (ring + work + dud > NOALLOC_SCRATCH_DOUBLES)
+    long long dud = h->prec == PSL1_PREC_FP64 ? 0 : (long long)(n + 1) * I.K;
+    const long long need = noalloc_round(ring) + noalloc_round(work) + dud;
+    if (need > NOALLOC_SCRATCH_DOUBLES)
         return fail(h, PSL1_ERR_ARG,
-                    "instance %d needs %lld doubles of scratch (m*K = %lld, factor %lld, coarse differences "
-                    "%lld); the fixed allocation-free array holds %lld",
-                    b, ring + work + dud, ring, work, dud, NOALLOC_SCRATCH_DOUBLES);
+                    "instance %d needs %lld doubles of scratch (history ring %lld, factor or 2D arrays %lld, "
+                    "coarse differences %lld, regions 256-byte aligned); the fixed allocation-free array holds %lld",
+                    b, need, ring, work, dud, NOALLOC_SCRATCH_DOUBLES);
     TRY(reset_status(h));
-    CU(h, launch_one_slice_noalloc(h->pa, b, n, d_U, d_V, ring, work, dud, h->stream));
+    CU(h, launch_one_slice_noalloc(h->pa, h->d_noalloc, b, n, d_U, d_V, ring, work, dud, h->stream));
     return check_device_status(h);
 }
 
@@ -1410,6 +1817,9 @@ psl1_status psl1_set_coarse(psl1_h h, psl1_mlp_h mh)
         return PSL1_OK;
     }
     if (h->pa.dim2) return fail(h, PSL1_ERR_ARG, "the learned coarse correction is defined for 1D instances");
+    for (int b = 0; b < h->B; ++b)
+        if (h->inst[b].basis == PSL1_BASIS_CHEB)
+            return fail(h, PSL1_ERR_ARG, "the learned coarse correction is defined for sine-basis instances");
     if (mh->stream != h->stream) CU(h, cudaStreamSynchronize(mh->stream));
     h->pa.mlp = mh->dev();
     if (h->par_graph) {   // the graph holds the kernels' arguments

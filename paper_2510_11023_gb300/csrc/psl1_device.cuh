@@ -17,6 +17,8 @@ constexpr int NT = 256;          // threads per CTA of the step kernels
 constexpr int KMAX_1D = 512;     // largest 1D mode count handled by one CTA
 constexpr int MMAX_2D = 64;      // largest 2D mode count per axis (K = Mx My <= 4096)
 constexpr int TILE = 32;         // Cholesky block size (one warp per panel)
+constexpr int CHEB_NMAX = 64;    // most collocation intervals (the step's shared-memory LU system)
+constexpr float INNER_RTOL_DEFAULT = 1e-7f;   // FP32 inner CG tolerance of the refined mixed step (tunable)
 
 // elements of a block-packed lower triangle of nb x nb blocks with row stride ldb
 __host__ __device__ constexpr int bp_elems(int nb, int ldb) { return nb * (nb + 1) / 2 * TILE * ldb; }
@@ -40,6 +42,12 @@ struct InstDev {
     int Qy, Qhy, tabY;           // y axis (2D): nodes, mirror pairs, table set
     int f_df;                    // f has no manufactured source term (double-float evaluation)
     float dpf[16], fpf[16];      // dpar, fpar as double-float pairs (hi, lo)
+    int soeL;                    // exponentials of the fast uniform history (0: none)
+    long long oS;                // offset in the exponential pool: exp(-s) [L], exp(-s nloc) [L], w [L]
+    long long oY;                // offset in the exponential-state pool (L x K)
+    int basis;                   // 0 sine Galerkin, 1 Chebyshev-Lobatto collocation (Mx intervals, K = Mx - 1)
+    long long oC;                // collocation: offset in the collocation pool (nodes, sines, Dm)
+    float inner_rtol;            // relative residual of the FP32 inner CG in the refined mixed step
 };
 
 struct TabDev {

@@ -124,6 +124,12 @@ __device__ __forceinline__ df inv_fact(int n) { return {kInvFact[n][0], kInvFact
 // three-float split of pi/2 (each product n * part exact by FMA), then the
 // Taylor series of sin and cos on |r| <= pi/4, truncated after r^17 / 17! and
 // r^16 / 16! (next terms below 1e-17 there), summed by Horner in r^2.
+// Valid range: |u| <= 2^20.  There n < 2^20, the products n P1, n P2 are exact
+// and n P3 is off by at most n 2^-73, so the reduced argument carries an
+// absolute error of about |u| 2^-48 -- the resolution of the double-float
+// input itself.  Beyond 2^20 the split no longer covers the product's bits
+// (and rintf stops being exact at 2^24); the solution values of this solver
+// are O(1) and the coefficient families are evaluated at them.
 __device__ __forceinline__ void df_sincos(df u, df& sn, df& cs)
 {
     constexpr double PIO2 = 1.5707963267948966;

@@ -14,6 +14,7 @@
 #include "psl1_step.cuh"
 #include "psl1_step_mixed.cuh"
 #include "psl1_step2d.cuh"
+#include "psl1_step_cheb.cuh"
 
 namespace psl1 {
 
@@ -24,6 +25,7 @@ struct Carve {
     PcgSmem cg;
     df *mz, *mh0, *mh1;      // learned-correction features and hidden activations (double-float)
     Step2D s2;               // 2D working arrays
+    ChebSmem ch;             // collocation step
 };
 
 template <typename T>
@@ -112,11 +114,17 @@ __device__ __forceinline__ Carve carve(const PathArgs& a, char* base)
     c.mz = at<df>(base, L.mz);
     c.mh0 = at<df>(base, L.mh0);
     c.mh1 = at<df>(base, L.mh1);
+    c.ch.M = at<double>(base, L.cm);
+    c.ch.u = at<double>(base, L.cu);
+    c.ch.Dc = at<double>(base, L.cdc);
+    c.ch.r = at<double>(base, L.cr);
+    c.ch.l = at<double>(base, L.cl);
+    c.ch.piv = at<int>(base, L.cpiv);
     return c;
 }
 
 // Shared-memory layout of the 1D step kernels.  Regions are 16-byte aligned.
-SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax)
+SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int Kc)
 {
     SmemLayout L;
     int off = 0;
@@ -163,6 +171,13 @@ SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax)
     L.mz = take(8 * (size_t)MLP_MAX_IN);
     L.mh0 = take(8 * (size_t)MLP_MAX_WIDTH);
     L.mh1 = take(8 * (size_t)MLP_MAX_WIDTH);
+    const bool ch = Kc > 0;   // collocation: dense K x K system, nodal vectors of n + 1 = K + 2
+    L.cm = ch ? take(8 * (size_t)Kc * Kc) : -1;
+    L.cu = ch ? take(8 * (size_t)(Kc + 2)) : -1;
+    L.cdc = ch ? take(8 * (size_t)(Kc + 2)) : -1;
+    L.cr = ch ? take(8 * (size_t)Kc) : -1;
+    L.cl = ch ? take(8 * (size_t)Kc) : -1;
+    L.cpiv = ch ? take(16) : -1;
     L.total = off;
     return L;
 }
@@ -236,7 +251,7 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
         if (a.prec == 0)
             bad = step2d_fp64(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad);
         else
-            bad = step2d_mixed(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad, a.prec == 2);
+            bad = step2d_mixed(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad, a.prec == 2 || one_solve);
         // algorithmic FLOPs: each operator application is four folded one-axis
         // transforms, 4 (Mx My Qy/2 + Mx Qy Qx/2) multiply-adds; the set-up
         // (node values, load, diagonal) costs one application, the coefficient
@@ -248,6 +263,14 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
         }
         return bad;
     } else {
+        if (I.basis == 1) {   // Chebyshev-Lobatto collocation (FP64 handles only)
+            bad = step_cheb(I, a.cheb, c, hist, te, mu, out, cv.ch, cv.s.bad);
+            if (threadIdx.x == 0 && a.flops) {
+                const double K = I.K;
+                atomicAdd(a.flops + a.flop_slot, 2.0 * K * K * (K + 2) + 2.0 * K * K * K / 3.0 + 2.0 * K * K);
+            }
+            return bad;
+        }
         if (a.prec == 0) {
             BPack<double, TILE> A{a.work + (size_t)blockIdx.x * a.work_stride};
             bad = step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
@@ -733,6 +756,78 @@ k_uni_step(PathArgs a, double* Wcur, double* dW, double* Us, int j, const double
     }
 }
 
+// One step j of the uniform scheme with the fast history (psl1_soe.cu): the
+// weights b(j - l) of the last nloc - 1 differences are exact, the older ones
+// are sums of exponentials, carried as the state
+//   Y_i(j) = sum_{l <= j - nloc} exp(-s_i (j - l)) dW_l,
+//   Y_i(j) = exp(-s_i) Y_i(j-1) + exp(-s_i nloc) dW_{j - nloc}   (updated here),
+// so that hist = W_j - sum_{j-l < nloc} b(j-l) dW_l - sum_i w_i Y_i(j).  The state
+// and its update are FP64 (L x K per instance, L2-resident); each step costs
+// O((nloc + L) K) instead of O(j K).
+template <bool D2>
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_uni_soe_step(PathArgs a, double* Wcur, double* dW, double* Us, int j, const double* soe, double* Y, int nloc)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve<D2>(a, smem_raw);
+    const int ii = blockIdx.x, tid = threadIdx.x;
+    const InstDev& I = a.inst[ii];
+    if (j >= I.N) return;
+    const int K = I.K, L = I.soeL;
+    const double* bF = a.bp + I.oB;
+    const double* dec = soe + I.oS;
+    const double* inj = dec + L;
+    const double* w = inj + L;
+    double* Yb = Y + I.oY;
+    const bool dfh = a.prec != 0;   // FP32-pipe paths store the differences as double-float pairs
+    const double* dWb = dW + I.oW;
+    auto diff = [&](int l, int k) -> double {
+        return dfh ? df_to_double(reinterpret_cast<const df*>(dWb)[(size_t)l * K + k]) : dWb[(size_t)l * K + k];
+    };
+    const int l0 = j - nloc + 1 > 0 ? j - nloc + 1 : 0;
+    for (int k = tid; k < K; k += NT) {
+        const double c = Wcur[I.oK + k];
+        double h = c;
+        for (int l = l0; l < j; ++l) h -= bF[j - l] * diff(l, k);
+        if (j >= nloc && L > 0) {
+            const double d = diff(j - nloc, k);
+            double acc0 = 0.0, acc1 = 0.0;
+            int i = 0;
+            for (; i + 1 < L; i += 2) {
+                const double y0 = fma(dec[i], Yb[(size_t)i * K + k], inj[i] * d);
+                const double y1 = fma(dec[i + 1], Yb[(size_t)(i + 1) * K + k], inj[i + 1] * d);
+                Yb[(size_t)i * K + k] = y0;
+                Yb[(size_t)(i + 1) * K + k] = y1;
+                acc0 = fma(w[i], y0, acc0);
+                acc1 = fma(w[i + 1], y1, acc1);
+            }
+            if (i < L) {
+                const double y0 = fma(dec[i], Yb[(size_t)i * K + k], inj[i] * d);
+                Yb[(size_t)i * K + k] = y0;
+                acc0 = fma(w[i], y0, acc0);
+            }
+            h -= acc0 + acc1;
+        }
+        cv.cur[k] = c;
+        cv.hist[k] = h;
+    }
+    if (tid == 0 && a.flops) atomicAdd(a.flops + a.flop_slot, 2.0 * K * ((j - l0) + (j >= nloc ? 2.0 * L : 0.0)));
+    __syncthreads();
+    int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dt * j, I.mu, cv.nxt, cv);
+    if (bad >= 0 && tid == 0) report(a.status, -2, ii, WHERE_UNI, j);
+    check_finite(a, cv.nxt, K, ii, WHERE_UNI, j);
+    const bool node = ((j + 1) % I.m) == 0;
+    for (int k = tid; k < K; k += NT) {
+        const double x = cv.nxt[k];
+        if (dfh)
+            reinterpret_cast<df*>(dW + I.oW)[(size_t)j * K + k] = df_from_double(x - cv.cur[k]);
+        else
+            dW[I.oW + (size_t)j * K + k] = x - cv.cur[k];
+        Wcur[I.oK + k] = x;
+        if (node) Us[I.oU + (size_t)((j + 1) / I.m) * K + k] = x;
+    }
+}
+
 template <bool D2>
 __global__ void __launch_bounds__(NT, D2 ? 1 : 2)
 k_one_step(PathArgs a, int ii, const double* c, const double* hist, double te, double mu, double* out)
@@ -831,11 +926,13 @@ static cudaError_t launch_k(void (*k)(KA...), dim3 grid, size_t smem, cudaStream
 // For callers that must not allocate device memory while they run (a real-time
 // loop whose memory was planned up front, or code running under an allocator
 // that forbids new device allocations): the single-slice fine propagator with
-// its scratch -- the fine-history ring and, where the factor does not sit in
-// shared memory, the factor workspace -- taken from this fixed array instead of
-// the handle's per-slot pools.  Every element of the scratch is written before
-// it is read, so nothing has to be cleared between calls; all calls share the
-// array, so calls that overlap on the GPU race.
+// its scratch taken from this fixed array instead of the handle's per-slot
+// pools.  The scratch is the fine-history ring (m K doubles), then the
+// FP64 1D factor or the 2D working arrays that do not fit in shared memory,
+// then the coarse differences of the FP32-pipe paths ((n+1) K double-float
+// pairs); each region starts on a 256-byte boundary.  Every element of the
+// scratch is written before it is read, so nothing has to be cleared between
+// calls; all calls share the array, so calls that overlap on the GPU race.
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
 template <bool D2>
@@ -848,31 +945,33 @@ k_one_slice_noalloc(PathArgs a, int ii, int n, const double* U, double* V)
     fine_slice<D2>(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring);
 }
 
-namespace {
-constexpr int kMaxDevices = 64;
-double* g_noalloc_addr[kMaxDevices] = {};
-}  // namespace
+// Device address of the fixed array on the current device.  Host code cannot
+// use the array's name as a device pointer (it names a host-side stand-in), so
+// the address is looked up here, with the device current, and kept by the
+// caller (psl1_create keeps it in the handle).  The lookup also loads this
+// file's kernel module on the device, which is when the array is placed.
+cudaError_t noalloc_scratch_address(double** p)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *p = static_cast<double*>(q);
+    return cudaSuccess;
+}
 
-cudaError_t launch_one_slice_noalloc(const PathArgs& a, int b, int n, const double* U, double* V,
+cudaError_t launch_one_slice_noalloc(const PathArgs& a, double* scratch, int b, int n, const double* U, double* V,
                                      long long ring_doubles, long long work_doubles, long long dud_doubles,
                                      cudaStream_t s)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_noalloc_addr[dev]) {   // once per device, with that device current
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = static_cast<double*>(p);
-    }
+    if (!scratch) return cudaErrorInvalidDevicePointer;
+    const long long ring_r = noalloc_round(ring_doubles), work_r = noalloc_round(work_doubles);
+    if (ring_r + work_r + dud_doubles > NOALLOC_SCRATCH_DOUBLES) return cudaErrorInvalidValue;
     PathArgs a2 = a;
-    a2.ring = g_noalloc_addr[dev];
-    a2.ring_stride = ring_doubles;
-    a2.work = g_noalloc_addr[dev] + ring_doubles;
-    a2.work_stride = work_doubles;
-    a2.dud = reinterpret_cast<df*>(g_noalloc_addr[dev] + ring_doubles + work_doubles);
+    a2.ring = scratch;
+    a2.ring_stride = ring_r;
+    a2.work = scratch + ring_r;
+    a2.work_stride = work_r;
+    a2.dud = reinterpret_cast<df*>(scratch + ring_r + work_r);
     a2.dud_stride = dud_doubles;
     a2.nslots = 1;
     size_t sm = step_smem_bytes(a2);
@@ -929,6 +1028,13 @@ cudaError_t launch_uni_step(const PathArgs& a, int B, double* Wcur, double* dW, 
 {
     size_t sm = step_smem_bytes(a);
     return LAUNCH_STEP_KERNEL(k_uni_step, B, sm, s, slot(a, 2), Wcur, dW, Us, j, part, chunk, maxchunks);
+}
+
+cudaError_t launch_uni_soe_step(const PathArgs& a, int B, double* Wcur, double* dW, double* Us, int j,
+                                const double* soe, double* Y, int nloc, cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    return LAUNCH_STEP_KERNEL(k_uni_soe_step, B, sm, s, slot(a, 2), Wcur, dW, Us, j, soe, Y, nloc);
 }
 
 cudaError_t launch_one_step(const PathArgs& a, int b, const double* c, const double* hist, double te, double mu,

@@ -24,6 +24,7 @@ struct SmemLayout {
     int cgx, cgr, cgp, cgq, cgpl, cgdinv, cgred, cggs, cggh, cgpart;   // PCG inner solver
     int mpart;                                                   // split-transform partial sums
     int mz, mh0, mh1;                                            // learned correction inference
+    int cm, cu, cdc, cr, cl, cpiv;                               // collocation step (FP64)
     int total;
 };
 
@@ -68,10 +69,12 @@ struct PathArgs {
     int dim2;                // 2D instances (the 2D layout below applies)
     Layout2D L2;
     const double* incr;      // last parareal increment e_k per instance (written by the correction sweep)
-    double loose_above;      // > 0: inexact F stage while e_k > loose_above (1D MIXED only; 0: off)
+    double loose_above;      // > 0: inexact F stage while e_k > loose_above (MIXED only; 0: off)
+    const double* cheb;      // collocation pool (nodes, sines, derivative matrices), may be null
 };
 
-SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax);
+// Kc: largest collocation K of the batch (0: none)
+SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int Kc = 0);
 
 size_t step_smem_bytes(const PathArgs& a);
 
@@ -92,6 +95,9 @@ cudaError_t launch_uni_hist(const PathArgs& a, int B, const double* dW, int j, d
                             int maxchunks, cudaStream_t s);
 cudaError_t launch_uni_step(const PathArgs& a, int B, double* Wcur, double* dW, double* Us, int j,
                             const double* part, int chunk, int maxchunks, cudaStream_t s);
+// Uniform scheme with the fast (sum-of-exponentials) history: one launch per fine step j.
+cudaError_t launch_uni_soe_step(const PathArgs& a, int B, double* Wcur, double* dW, double* Us, int j,
+                                const double* soe, double* Y, int nloc, cudaStream_t s);
 // Single pieces (one CTA).
 cudaError_t launch_one_step(const PathArgs& a, int b, const double* c, const double* hist, double te,
                             double mu, double* out, cudaStream_t s);
@@ -117,7 +123,11 @@ cudaError_t launch_pr_update(const double* incr, int* active, int* nfirst, int* 
 
 // Single slice with scratch from a fixed device array (no allocation).
 constexpr long long NOALLOC_SCRATCH_DOUBLES = 512 * 1024;   // 4 MiB
-cudaError_t launch_one_slice_noalloc(const PathArgs& a, int b, int n, const double* U, double* V,
+// regions of the fixed array start on 256-byte (32-double) boundaries
+constexpr long long noalloc_round(long long doubles) { return (doubles + 31) / 32 * 32; }
+// device address of the fixed array on the current device (loads its module there)
+cudaError_t noalloc_scratch_address(double** p);
+cudaError_t launch_one_slice_noalloc(const PathArgs& a, double* scratch, int b, int n, const double* U, double* V,
                                      long long ring_doubles, long long work_doubles, long long dud_doubles,
                                      cudaStream_t s);
 

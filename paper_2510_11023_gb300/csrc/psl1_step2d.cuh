@@ -509,7 +509,7 @@ __device__ void pcg2d(const Dims2& g, const Tabs2<Nm>& tb, typename Nm::V mu, co
 }
 
 constexpr int PCG2_MAXIT32 = 60;
-constexpr float PCG2_RTOL32 = 1e-7f;
+constexpr float PCG2_RTOL32 = INNER_RTOL_DEFAULT;
 constexpr int PCG2_MAXIT64 = 1000;
 constexpr double PCG2_RTOL64 = 1e-14;
 
@@ -631,7 +631,8 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
         S.z[k] = (float)rk;
     }
     __syncthreads();
-    pcg2d<NumF, 2, 4, 4>(g, tf, (float)mu, S.wd32, S.z, S, flag, PCG2_MAXIT32, PCG2_RTOL32);
+    const float rtol = fp32_only ? PCG2_RTOL32 : I.inner_rtol;   // tunable in the refined step
+    pcg2d<NumF, 2, 4, 4>(g, tf, (float)mu, S.wd32, S.z, S, flag, PCG2_MAXIT32, rtol);
     float zprev = 0.f;
     for (int sweep = 0;; ++sweep) {
         float zmax = 0.f, xmax = 0.f;
@@ -656,7 +657,7 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
         for (int k = tid; k < K; k += NT)
             S.z[k] = (float)(S.rhs[k] - S.xr[k] - mu * df_to_double(S.cdf[k]));
         __syncthreads();
-        pcg2d<NumF, 2, 4, 4>(g, tf, (float)mu, S.wd32, S.z, S, flag, PCG2_MAXIT32, PCG2_RTOL32);
+        pcg2d<NumF, 2, 4, 4>(g, tf, (float)mu, S.wd32, S.z, S, flag, PCG2_MAXIT32, rtol);
     }
     for (int k = tid; k < K; k += NT) out[k] = S.xr[k];
     __syncthreads();

@@ -335,7 +335,7 @@ __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const do
 // has condition number about D_+/D_-, so a few iterations reduce the residual
 // by FP32's resolution.  r: ms.z on entry; result in ms.z.
 constexpr int PCG_MAXIT = 40;
-constexpr float PCG_RTOL = 1e-7f;
+constexpr float PCG_RTOL = INNER_RTOL_DEFAULT;
 // Refinement stops when the last correction is below REFINE_TOL of the
 // iterate, or when the contraction it shows (rho = |z_k| / |z_{k-1}|) puts the
 // next correction, rho |z_k|, below REFINE_EST of the iterate.
@@ -553,7 +553,9 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
     }
     if (tid == 0) *s.bad = -1;
     __syncthreads();
-    pcg32(I, mu, ms, cg, PCG_MAXIT, PCG_RTOL);
+    // inner tolerance: the FP32 step's own; the refined step's is tunable per instance
+    const float rtol = fp32_only ? PCG_RTOL : I.inner_rtol;
+    pcg32(I, mu, ms, cg, PCG_MAXIT, rtol);
     float zprev = 0.f;
     for (int sweep = 0;; ++sweep) {
         float zmax = 0.f, xmax = 0.f;
@@ -572,7 +574,7 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
         zprev = zmax;
         if (tid == 0) ms.flag[2] += 1;
         residual_df(I, mu, ms);
-        pcg32(I, mu, ms, cg, PCG_MAXIT, PCG_RTOL);
+        pcg32(I, mu, ms, cg, PCG_MAXIT, rtol);
     }
     for (int k = tid; k < I.K; k += NT) out[k] = ms.x[k];
     __syncthreads();

@@ -18,7 +18,8 @@ from . import build as _build
 from .workloads import InstanceSpec, Workload
 
 PREC = {"fp64": 0, "mixed": 1, "fp32": 2}
-SERIAL = {"hybrid": 0, "uniform": 1, "coarse": 2}
+SERIAL = {"hybrid": 0, "uniform": 1, "coarse": 2, "uniform-soe": 3}
+BASIS = {"sine": 0, "cheb": 1}
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOT_SPD", -3: "ERR_NONFINITE", -4: "ERR_CUDA", -5: "ERR_TIMEOUT",
           -6: "ERR_NOT_CONVERGED", -7: "ERR_STATE", -8: "ERR_NOMEM"}
 
@@ -37,7 +38,7 @@ class Instance(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("modes", ctypes.c_int * 2), ("qnodes", ctypes.c_int * 2),
                 ("nsteps", ctypes.c_int), ("alpha", ctypes.c_double), ("T", ctypes.c_double),
                 ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2),
-                ("dpar", ctypes.c_double * 8), ("fpar", ctypes.c_double * 8)]
+                ("dpar", ctypes.c_double * 8), ("fpar", ctypes.c_double * 8), ("basis", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -72,6 +73,11 @@ SIGNATURES = {
     "psl1_set_inexact_fine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "psl1_get_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D]),
     "psl1_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
+    "psl1_get_soe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, _D, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int)]),
+    "psl1_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, _I]),
+    "psl1_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _F, _I]),
+    "psl1_assemble": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _F, _F]),
     "psl1_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, _D, _D]),
     "psl1_fine_slice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D]),
     "psl1_coarse_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D]),
@@ -144,6 +150,7 @@ def to_instance(s: InstanceSpec) -> Instance:
     fp = list(s.fpar) + [0.0] * (8 - len(s.fpar))
     for i in range(8):
         c.dpar[i], c.fpar[i] = dp[i], fp[i]
+    c.basis = BASIS[s.basis]
     return c
 
 
@@ -291,6 +298,35 @@ class Problem:
         V = np.zeros((m + 1, self.K[b]))
         _chk(self.L.psl1_fine_slice(self.h, b, n, _dp(U), _dp(V)), self.h)
         return V
+
+    def assemble(self, b: int, D, method: str = "tensor"):
+        """Dense stiffness matrices (units x K x K, FP32) from nodal D (units x Q,
+        ascending nodes); returns (A, device ms of the assembly kernel)."""
+        D = np.ascontiguousarray(np.atleast_2d(D), dtype=np.float64)
+        units, K = D.shape[0], self.K[b]
+        A = np.zeros((units, K, K), dtype=np.float32)
+        ms = ctypes.c_float(0.0)
+        _chk(self.L.psl1_assemble(self.h, b, {"tensor": 0, "moments": 1}[method], units, _dp(D),
+                                  A.ctypes.data_as(_F), ctypes.byref(ms)), self.h)
+        return A, ms.value
+
+    def autotune(self, cache_path: str | None = None) -> bool:
+        """Tune the F stage (see psl1_autotune); True if every choice came from the cache."""
+        fc = ctypes.c_int(0)
+        _chk(self.L.psl1_autotune(self.h, cache_path.encode() if cache_path else None, ctypes.byref(fc)), self.h)
+        return bool(fc.value)
+
+    def tuning(self, b: int = 0) -> dict:
+        r, g = ctypes.c_float(0), ctypes.c_int(0)
+        _chk(self.L.psl1_get_tuning(self.h, b, ctypes.byref(r), ctypes.byref(g)), self.h)
+        return {"inner_rtol": r.value, "fstage_ctas": g.value}
+
+    def get_soe(self, b: int):
+        """Exponents s and weights w of instance b's fast history."""
+        n = ctypes.c_int(0)
+        s, w = np.zeros(512), np.zeros(512)
+        _chk(self.L.psl1_get_soe(self.h, b, _dp(s), _dp(w), 512, ctypes.byref(n)), self.h)
+        return s[: n.value], w[: n.value]
 
     def fine_slice_noalloc(self, b: int, n: int, d_U: int, d_V: int) -> None:
         """F_n on caller-owned device arrays (pointers), without any allocation."""

@@ -30,9 +30,12 @@ class InstanceSpec:
     hi: tuple = (1.0, 1.0)
     dpar: tuple = (1.0, 0.5, 0, 0, 0, 0, 0, 0)
     fpar: tuple = (0.1, 0, 0, 0, 0, 0, 0, 0)
+    basis: str = "sine"             # "sine" (Galerkin, modes) or "cheb" (collocation, modes[0] intervals)
 
     @property
     def K(self) -> int:
+        if self.basis == "cheb":
+            return self.modes[0] - 1
         return self.modes[0] * (self.modes[1] if self.dim == 2 else 1)
 
     @property
@@ -130,6 +133,18 @@ def e1(K: int = 16, P: int = 256, m: int = 32, alpha: float = 0.5) -> Workload:
     spec = InstanceSpec(modes=(K, 1), nsteps=P * m, alpha=alpha, dpar=(1.0, 0, 1.0, 0, 0, 0, 0, 0),
                         fpar=(0, 0, 0, 1.0, 0, 0, 0, 0))
     return Workload("paper E1 shape K=%d P=%d m=%d" % (K, P, m), P, [spec], [u0])
+
+
+def e1_collocation(n: int = 16, P: int = 256, m: int = 32, alpha: float = 0.5) -> Workload:
+    """The paper's model problem with its own spatial scheme (Sec. 4.1-4.2):
+    Chebyshev-Lobatto collocation on n = 2^4 intervals of [0,1], D = 1 + u,
+    f = sin(pi x) e^{-t}, u0 = x^4 (1-x)^4 sampled at the interior nodes
+    x_j = (1 + cos(j pi/n))/2, j = 1..n-1, alpha = 0.5, P = 2^8, m = 2^5."""
+    x = 0.5 * (1.0 + np.cos(np.arange(1, n) * math.pi / n))
+    u0 = x**4 * (1 - x) ** 4
+    spec = InstanceSpec(modes=(n, 1), nsteps=P * m, alpha=alpha, dpar=(1.0, 0, 1.0, 0, 0, 0, 0, 0),
+                        fpar=(0, 0, 0, 1.0, 0, 0, 0, 0), basis="cheb")
+    return Workload("paper model problem, collocation n=%d P=%d m=%d" % (n, P, m), P, [spec], [u0])
 
 
 def _u0_2d(rng, Mx: int, My: int) -> np.ndarray:

@@ -81,3 +81,26 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(psl1.PSL1Error) as ei:
         psl1.Problem(workloads.cfg1())
     assert ei.value.status == -4
+
+
+def test_invalid_collocation_arguments_rejected_before_device_use():
+    L = psl1.load()
+    h = ctypes.c_void_p()
+    spec = workloads.e1_collocation(P=4, m=2).specs[0]
+
+    def create(inst, prec=0):
+        arr = (psl1.Instance * 1)(inst)
+        return L.psl1_create(ctypes.byref(h), 1, arr, 4, prec, None)
+
+    bad = psl1.to_instance(spec)
+    bad.modes[0] = 65                      # more than 64 collocation intervals
+    assert create(bad) == -1 and b"collocation" in L.psl1_last_error(None)
+    bad = psl1.to_instance(spec)
+    bad.dim = 2                            # collocation is 1D
+    bad.modes[1] = 4
+    assert create(bad) == -1
+    bad = psl1.to_instance(spec)
+    bad.basis = 7                          # unknown scheme
+    assert create(bad) == -1 and b"basis" in L.psl1_last_error(None)
+    assert create(psl1.to_instance(spec), prec=1) == -1   # collocation runs in FP64 only
+    assert b"FP64" in L.psl1_last_error(None)

@@ -1,4 +1,4 @@
-"""Inexact early parareal iterations (psl1_set_inexact_fine, MIXED 1D).
+"""Inexact early parareal iterations (psl1_set_inexact_fine, MIXED, 1D and 2D).
 
 While an instance's last increment is above the threshold, the F stage of
 iteration k runs slices n > k with one FP32 inner solve per fine step; slice
@@ -88,3 +88,26 @@ def test_inexact_threshold_rejects_bad_values():
             with pytest.raises(psl1.PSL1Error) as ei:
                 pr.set_inexact_fine(bad)
             assert ei.value.status == -1
+
+
+def test_inexact_2d_exact_prefix_and_fixed_point():
+    # 2D: the inexact slices take the FP32 2D step (one FP32 CG solve, no refinement);
+    # the exact prefix and the fixed point S_hyb survive, as in 1D
+    wl = workloads.small_batch_2d()
+    with psl1.Problem(wl, precision="mixed") as pr:
+        pr.solve_serial("hybrid")
+        S = pr.get_coeffs("serial")
+        pr.set_inexact_fine(1e-300)
+        pr.keep_iterates(True)
+        k = pr.solve_parareal(tol=0.0)
+        assert k == wl.P
+        for j in range(k + 1):
+            Uj = pr.get_iterate(j)
+            for b in range(wl.B):
+                assert np.abs(Uj[b][: j + 1] - S[b][: j + 1]).max() <= 1e-13 * np.abs(S[b]).max(), (j, b)
+        pr.set_inexact_fine(1e-4)
+        pr.keep_iterates(False)
+        pr.solve_parareal(tol=1e-12)
+        U = pr.get_coeffs("parareal")
+    for b in range(wl.B):
+        assert rel(U[b], S[b]) < TOL_SOLVE, b
