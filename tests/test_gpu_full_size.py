@@ -26,7 +26,9 @@ TOL = 1e-10
 
 def _samples(wl):
     """(instance, slice) pairs: the largest K, the longest slice, an alpha = 1
-    instance, and one more; first, middle and last slices among them."""
+    instance, and one more; first, middle and last slices among them; and two
+    instances with K >= 250 and the smallest alpha (the largest mu = dt^a
+    Gamma(2-a), the worst-conditioned steps), late slices."""
     K = np.array([s.K for s in wl.specs])
     m = np.array([s.nsteps // wl.P for s in wl.specs])
     a = np.array([s.alpha for s in wl.specs])
@@ -35,7 +37,10 @@ def _samples(wl):
     be = int(np.flatnonzero(a == 1.0)[0])
     other = int(np.argmin(K))
     P = wl.P
-    return [(big_k, P - 1), (long_m, 0), (long_m, P // 2), (be, 3 * P // 4), (other, 1), (other, P - 1)]
+    hard = np.flatnonzero((K >= 250) & (a == a.min()))
+    hard = hard[np.argsort(m[hard])][:2]             # the two shortest slices among them (oracle time)
+    return [(big_k, P - 1), (long_m, 0), (long_m, P // 2), (be, 3 * P // 4), (other, 1), (other, P - 1)] + \
+        [(int(hard[0]), P - 2), (int(hard[1]), P // 2 + 7)]
 
 
 @pytest.mark.parametrize("inexact", [0.0, 1e-5])
