@@ -67,8 +67,9 @@ def parse():
                     help="CPU seconds per reference-arm step (0: about 2 minutes in total)")
     ap.add_argument("--no-ref-context", action="store_true",
                     help="reference arm: skip the oracle's whole solves of the small configurations")
-    ap.add_argument("--coarse", default="auto", choices=["auto", "l1", "learned"],
-                    help="coarse propagator; auto: the faster to rel err 1e-8 in warm-up")
+    ap.add_argument("--coarse", default="auto", choices=["auto", "l1", "l1x2", "l1x4", "learned"],
+                    help="coarse propagator: the one-step L1 G, the L1 G with 2 or 4 substeps per slice, or the "
+                         "learned correction; auto: the fastest to rel err 1e-8 in warm-up")
     ap.add_argument("--inexact", default="auto", choices=["auto", "on", "off"],
                     help="inexact early iterations (the FP32 step on slices not yet exact while the increment "
                          "exceeds a threshold, 1e-4 or 1e-5; mixed); auto: the fastest to rel err 1e-8 in warm-up")
@@ -525,11 +526,18 @@ def main():
     stream = torch.cuda.current_stream()
     psl1.load()
     fp64_tf, fp32_tf = psl1.psl1_probe_peaks()
+    dmma_tf = psl1.psl1_probe_dmma()
 
     wl = make_workload(args, dist.rank)
     dim2 = wl.specs[0].dim == 2
-    if dim2:
-        args.coarse = "l1"          # the learned correction is defined for 1D instances
+    mmin = min(s.nsteps // wl.P for s in wl.specs)
+    substeps = {"l1": 1, "l1x2": 2, "l1x4": 4, "learned": 1}
+    if args.coarse == "auto":
+        coarse_list = [c for c in ("l1", "l1x2", "l1x4") if substeps[c] <= mmin]
+        if not dim2:                 # the learned correction is defined for 1D instances
+            coarse_list.append("learned")
+    else:
+        coarse_list = [args.coarse]
     u0 = wl.u0_concat()
     d_u0 = torch.from_numpy(u0).to("cuda")
     torch.cuda.synchronize()
@@ -569,7 +577,7 @@ def main():
     # learned coarse correction, trained offline (not timed) on another seed of the
     # same instance distribution from the pairs parareal computes
     mlp, train_info = None, None
-    if args.coarse in ("auto", "learned"):
+    if "learned" in coarse_list:
         t0 = time.perf_counter()
         twl = workloads.cfg2(B=args.train_batch, seed=args.seed + 7919 + dist.rank)
         with psl1.Problem(twl, precision=args.precision, stream=stream.cuda_stream) as data:
@@ -582,7 +590,10 @@ def main():
                       "seed": args.seed + 7919}
 
     def configure(coarse, inexact):
-        pr.set_coarse(mlp if coarse == "learned" else None)
+        pr.set_coarse(None)
+        pr.set_coarse_substeps(substeps[coarse])
+        if coarse == "learned":
+            pr.set_coarse(mlp)
         pr.set_inexact_fine(inexact)
 
     def timed_solve(tol_):
@@ -604,7 +615,7 @@ def main():
 
     # warm-up choices among configurations that reach the target error at the fixed rule:
     # the coarse propagator, then inexact early iterations (mixed 1D only)
-    cands = {c: trial(c) for c in (["l1", "learned"] if args.coarse == "auto" else [args.coarse])}
+    cands = {c: trial(c) for c in coarse_list}
     ok = [c for c in cands if cands[c]["rel_err"] <= TARGET] or list(cands)
     coarse = min(ok, key=lambda c: cands[c]["ms"])
     best = cands[coarse]
@@ -768,7 +779,9 @@ def main():
             "inexact_early_iterations": {"above": inexact, "candidates": inexact_cand},
             "serial_fp64_ms": serial_fp64_ms, "serial_ms": serial_ms, "serial_uniform": uniform,
             "speedup_vs_serial_fp64": serial_fp64_ms / ms_step, "speedup_vs_serial_same_precision": serial_ms / ms_step,
-            "measured_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf}, "wall_s": wall}
+            "measured_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf, "fp64_tensor": dmma_tf,
+                                      "source": "psl1_probe_peaks (FMA chains), psl1_probe_dmma (mma.sync f64)"},
+            "wall_s": wall}
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
     pr.close()

@@ -219,7 +219,20 @@ psl1_status psl1_set_graph(psl1_h h, int on);
  * its iteration, Eq. Parareal, uses the same F throughout).                 */
 psl1_status psl1_set_inexact_fine(psl1_h h, double above);
 
-/* Statistics of the last solve.                                             */
+/* Coarse propagator with c L1 substeps per slice (1 <= c <= the smallest m
+ * of the batch; 1, the default, is the paper's one-step G of Eq.
+ * CoarsePropagator).  G^(c)_n(U_{0:n}) is the fine propagator of Eq.
+ * FinePropagator on the grid with c steps per slice (dt_c = dT/c, the coarse
+ * history of Eq. L1Fine at r/c); c = m makes G the fine propagator itself.
+ * Parareal still converges to the sequential fine sweep S_hyb (Eq.
+ * PararealConvergence holds for any G); a finer G contracts faster per
+ * iteration and costs c times more in the sequential coarse sweep -- the
+ * coarse-fine balance the paper names as future work (Conclusion, item
+ * (ii)).  Rejected while a learned correction is attached (it is defined on
+ * the one-step G).  Rebuilds the parareal graph.                           */
+psl1_status psl1_set_coarse_substeps(psl1_h h, int c);
+
+/* Statistics of the last solve.                                             *//* Statistics of the last solve.                                             */
 psl1_status psl1_get_stats(psl1_h h, psl1_stats* st);
 
 /* Dense stiffness matrices of the 1D sine-basis instance b (Eq. AForm with
@@ -375,6 +388,10 @@ void psl1_mlp_destroy(psl1_mlp_h mh);
  * (dependent FMA chains on every SM, best of three timed launches).  Used
  * as the roofline denominators of the ALU-bound kernels.                    */
 psl1_status psl1_probe_peaks(double* fp64_tflops, double* fp32_tflops);
+/* Measured FP64 tensor-core (mma.sync m8n8k4 f64) throughput in TFLOP/s:
+ * four independent accumulators per warp, 8 CTAs of 256 threads per SM,
+ * best of three timed launches.                                             */
+psl1_status psl1_probe_dmma(double* fp64_tensor_tflops);
 
 const char* psl1_last_error(psl1_h h);
 void psl1_destroy(psl1_h h);

@@ -39,7 +39,7 @@ class Prob(ctypes.Structure):
         ("alpha", ctypes.c_double), ("T", ctypes.c_double),
         ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2),
         ("dpar", ctypes.c_double * 8), ("fpar", ctypes.c_double * 8),
-        ("solver", ctypes.c_int), ("basis", ctypes.c_int),
+        ("solver", ctypes.c_int), ("basis", ctypes.c_int), ("csub", ctypes.c_int),
     ]
 
     @property
@@ -150,13 +150,15 @@ def _out(*shape):
 
 def make_prob(*, dim=1, Mx, My=1, Qx=None, Qy=None, N, P, alpha, T=1.0, lo=(0.0, 0.0),
               hi=(1.0, 1.0), dpar=(1.0, 0.5, 0, 0, 0, 0, 0, 0), fpar=(0.1, 0, 0, 0, 0, 0, 0, 0),
-              solver: str = "cholesky", basis: str = "sine") -> Prob:
+              solver: str = "cholesky", basis: str = "sine", coarse_substeps: int = 1) -> Prob:
     """Problem record; Qx/Qy default to twice the modes (Gauss-Legendre).
     solver: "cholesky" (dense factor of the assembled matrix) or "cg"
     (conjugate gradients on the weak form, for mode counts whose assembly
     is out of reach); both solve the same SPD system of each step.
     basis: "sine" (Galerkin, Mx modes) or "cheb" (Chebyshev-Lobatto
-    collocation, 1D: Mx intervals, the Mx - 1 interior nodal values)."""
+    collocation, 1D: Mx intervals, the Mx - 1 interior nodal values).
+    coarse_substeps: L1 substeps per slice of the coarse propagator (1: the
+    paper's one-step G)."""
     p = Prob()
     p.dim, p.Mx = dim, Mx
     p.My = My if dim == 2 else 1
@@ -171,6 +173,7 @@ def make_prob(*, dim=1, Mx, My=1, Qx=None, Qy=None, N, P, alpha, T=1.0, lo=(0.0,
         p.dpar[i], p.fpar[i] = dp[i], fp[i]
     p.solver = {"cholesky": 0, "cg": 1}[solver]
     p.basis = {"sine": 0, "cheb": 1}[basis]
+    p.csub = int(coarse_substeps)
     if p.basis == 1 and dim != 1:
         raise ValueError("collocation is 1D")
     if N % P:

@@ -65,6 +65,8 @@ typedef struct {
                            1 conjugate gradients on the weak form (no matrix) */
     int basis;          /* space: 0 sine Galerkin (Mx modes), 1 Chebyshev-Lobatto
                            collocation (1D, Mx intervals, Mx - 1 interior values) */
+    int csub;           /* coarse propagator: 0 or 1 the one-step L1 G of the paper;
+                           c > 1: c L1 substeps per slice (see coarse_step)        */
 } orc_prob;
 
 /* ------------------------------------------------------------------------ */
@@ -855,9 +857,31 @@ int orc_mlp_features(const orc_prob* p, int nU, int nH, int n, const double* U, 
 /*       + mu_T (f(T_n,U_n),chi),   mu_T = dT^alpha Gamma(2-alpha).           */
 /* U holds U_0..U_n (row-major (n+1) x K).  mlp may be NULL.                 */
 /* ------------------------------------------------------------------------ */
+static int fine_slice(const orc_prob* p, const orc_disc* d, int n, const double* U, double* V);
+
+/* Coarse propagator with c > 1 substeps (the paper's outlook, Conclusion item
+ * (ii), coarse-fine strategies): G^(c)_n(U_{0:n}) is the fine propagator of
+ * Eq. FinePropagator on the grid with c steps per slice, i.e. F_n of the same
+ * problem with N = P c.  c = 1 is the one-step G below; c = m is F itself.
+ * Parareal converges to the sequential F sweep for any G.  With a learned
+ * correction attached, the one-step G it was defined on is used.           */
+static int coarse_substeps(const orc_prob* p, const orc_disc* d, int n, const double* U, double* out)
+{
+    orc_prob q = *p;
+    q.N = p->P * p->csub;
+    q.csub = 0;
+    double* V = malloc(sizeof(double) * (size_t)(p->csub + 1) * d->K);
+    if (!V) return -1000000;
+    int st = fine_slice(&q, d, n, U, V);
+    memcpy(out, V + (size_t)p->csub * d->K, sizeof(double) * d->K);
+    free(V);
+    return st;
+}
+
 static int coarse_step(const orc_prob* p, const orc_disc* d, int n, const double* U,
                        const orc_mlp* mlp, double* out)
 {
+    if (p->csub > 1 && !mlp) return coarse_substeps(p, d, n, U, out);
     int K = d->K;
     double dT = p->T / p->P;
     double muT = pow(dT, p->alpha) * orc_gamma2a(p->alpha);

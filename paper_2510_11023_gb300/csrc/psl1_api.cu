@@ -66,6 +66,8 @@ struct psl1_problem {
     double* d_noalloc = nullptr;  // device address of the library's fixed scratch array (not owned)
     double* d_cheb = nullptr;     // collocation pool: per instance nodes, sines and derivative matrix
     int fgrid = 0;                // F-stage CTAs chosen by psl1_autotune (0: one per slot)
+    double *d_bcc = nullptr, *d_bccd = nullptr;   // coarse-substep weights (FP64, double-float)
+    size_t bcc_cap = 0;
     // uniform solver pools (lazy)
     double *d_Wcur = nullptr, *d_dW = nullptr, *d_part = nullptr;
     int uni_chunk = 32, uni_maxchunks = 0;   // history rows per CTA of k_uni_hist (autotuned)
@@ -405,6 +407,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         I.dim = d.dim;
         I.basis = d.basis;
         I.inner_rtol = INNER_RTOL_DEFAULT;
+        I.mc = 1;
         I.Mx = d.modes[0];
         I.My = d.dim == 2 ? d.modes[1] : 1;
         I.K = I.basis == PSL1_BASIS_CHEB ? I.Mx - 1 : I.Mx * I.My;
@@ -1462,12 +1465,16 @@ struct psl1_mlp {
     int bcap = 0;
     float *X0 = nullptr, *T = nullptr, *Y = nullptr, *dY = nullptr, *dH = nullptr, *dH2 = nullptr;
     float *pre[3] = {nullptr, nullptr, nullptr}, *act[3] = {nullptr, nullptr, nullptr};
+    float *tA = nullptr, *tB = nullptr;   // transposes for the weight gradients
+    int* tc_status = nullptr;             // set by a tensor-core product whose bounded wait gave up
     int S = 0;                 // sample slots in Z / R
     int Scap = 0;
     float *Z = nullptr, *R = nullptr;
     int* valid = nullptr;      // indices of the slots holding samples
     int nvalid = 0;
     std::string err;
+
+    MlpTc tc() const { return {wT, tA, tB, tc_status}; }
 
     MlpDev dev() const
     {
@@ -1537,6 +1544,16 @@ static psl1_status ensure_batch(psl1_mlp* h, int B)
     for (int l = 0; l < 3; ++l) {
         TRY(malloc_m(h, &h->pre[l], (size_t)B * W));
         TRY(malloc_m(h, &h->act[l], (size_t)B * W));
+    }
+    const size_t wmax = std::max<size_t>(W, std::max(h->nin, h->nout));
+    TRY(malloc_m(h, &h->tA, (size_t)B * wmax));
+    TRY(malloc_m(h, &h->tB, (size_t)B * wmax));
+    if (!h->tc_status) {
+        float* st = nullptr;
+        TRY(malloc_m(h, &st, 1));
+        h->tc_status = reinterpret_cast<int*>(st);
+        if (cudaMemsetAsync(h->tc_status, 0, sizeof(int), h->stream) != cudaSuccess)
+            return mfail(h, PSL1_ERR_CUDA, "status word");
     }
     h->bcap = B;
     return PSL1_OK;
@@ -1631,15 +1648,29 @@ psl1_status psl1_mlp_set_params(psl1_mlp_h h, const float* params, const float* 
     return PSL1_OK;
 }
 
+// a tensor-core product of the network whose bounded barrier wait gave up
+static psl1_status check_tc(psl1_mlp* h)
+{
+    if (!h->tc_status) return PSL1_OK;
+    int st = 0;
+    MCU(h, cudaMemcpyAsync(&st, h->tc_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MCU(h, cudaStreamSynchronize(h->stream));
+    if (st) {
+        cudaMemsetAsync(h->tc_status, 0, sizeof(int), h->stream);
+        return mfail(h, PSL1_ERR_TIMEOUT, "tensor-core product: a bounded barrier wait gave up");
+    }
+    return PSL1_OK;
+}
+
 psl1_status psl1_mlp_forward(psl1_mlp_h h, int B, const float* z, float* y)
 {
     if (!h || !z || !y || B < 1) return mfail(h, PSL1_ERR_ARG, "bad argument");
     TRY(ensure_batch(h, B));
     MCU(h, cudaMemcpyAsync(h->X0, z, sizeof(float) * B * h->nin, cudaMemcpyHostToDevice, h->stream));
-    MCU(h, mlp_forward(h->X0, B, h->w16, h->master, h->L, h->pre, h->act, h->Y, h->stream));
+    MCU(h, mlp_forward(h->X0, B, h->w16, h->master, h->L, h->pre, h->act, h->Y, h->tc(), h->stream));
     MCU(h, cudaMemcpyAsync(y, h->Y, sizeof(float) * B * h->nout, cudaMemcpyDeviceToHost, h->stream));
     MCU(h, cudaStreamSynchronize(h->stream));
-    return PSL1_OK;
+    return check_tc(h);
 }
 
 psl1_status psl1_mlp_loss_grad(psl1_mlp_h h, int B, const float* z, const float* t, float* grad, float* loss)
@@ -1649,13 +1680,13 @@ psl1_status psl1_mlp_loss_grad(psl1_mlp_h h, int B, const float* z, const float*
     MCU(h, cudaMemcpyAsync(h->X0, z, sizeof(float) * B * h->nin, cudaMemcpyHostToDevice, h->stream));
     MCU(h, cudaMemcpyAsync(h->T, t, sizeof(float) * B * h->nout, cudaMemcpyHostToDevice, h->stream));
     MCU(h, cudaMemsetAsync(h->loss, 0, sizeof(float), h->stream));
-    MCU(h, mlp_forward(h->X0, B, h->w16, h->master, h->L, h->pre, h->act, h->Y, h->stream));
+    MCU(h, mlp_forward(h->X0, B, h->w16, h->master, h->L, h->pre, h->act, h->Y, h->tc(), h->stream));
     MCU(h, mlp_backward(h->X0, B, h->T, h->w16, h->L, h->pre, h->act, h->Y, h->dY, h->dH, h->dH2, h->grad, h->loss,
-                        h->stream));
+                        h->tc(), h->stream));
     if (grad) MCU(h, cudaMemcpyAsync(grad, h->grad, sizeof(float) * h->L.nparam, cudaMemcpyDeviceToHost, h->stream));
     if (loss) MCU(h, cudaMemcpyAsync(loss, h->loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     MCU(h, cudaStreamSynchronize(h->stream));
-    return PSL1_OK;
+    return check_tc(h);
 }
 
 psl1_status psl1_mlp_adam_step(psl1_mlp_h h, const float* grad, float lr)
@@ -1774,9 +1805,9 @@ psl1_status psl1_mlp_train(psl1_mlp_h mh, psl1_h data, int epochs, int batch, fl
             float lr_t = 0.5f * lr * (1.0f + cosf(3.14159265f * (float)it / (float)std::max<long long>(total, 1)));
             MCU(mh, mlp_gather(mh->Z, mh->R, mh->valid, S, mh->nin, mh->nout, batch, pa, pc, (long long)s * batch,
                                mh->X0, mh->T, mh->stream));
-            MCU(mh, mlp_forward(mh->X0, batch, mh->w16, mh->master, mh->L, mh->pre, mh->act, mh->Y, mh->stream));
+            MCU(mh, mlp_forward(mh->X0, batch, mh->w16, mh->master, mh->L, mh->pre, mh->act, mh->Y, mh->tc(), mh->stream));
             MCU(mh, mlp_backward(mh->X0, batch, mh->T, mh->w16, mh->L, mh->pre, mh->act, mh->Y, mh->dY, mh->dH,
-                                 mh->dH2, mh->grad, mh->loss, mh->stream));
+                                 mh->dH2, mh->grad, mh->loss, mh->tc(), mh->stream));
             mh->adam_t += 1;
             MCU(mh, mlp_adam(mh->master, mh->grad, mh->m, mh->v, mh->L.nparam, mh->adam_t, lr_t, 0.9f, 0.999f, 1e-8f,
                              mh->stream));
@@ -1790,6 +1821,54 @@ psl1_status psl1_mlp_train(psl1_mlp_h mh, psl1_h data, int epochs, int batch, fl
         }
     }
     MCU(mh, cudaStreamSynchronize(mh->stream));
+    return check_tc(mh);
+}
+
+psl1_status psl1_set_coarse_substeps(psl1_h h, int c)
+{
+    if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
+    int mmin = h->inst[0].m;
+    for (int b = 0; b < h->B; ++b) mmin = std::min(mmin, h->inst[b].m);
+    if (c < 1 || c > mmin) return fail(h, PSL1_ERR_ARG, "coarse substeps must be in [1, %d] (the smallest m)", mmin);
+    if (c > 1 && h->pa.mlp.on)
+        return fail(h, PSL1_ERR_ARG, "the learned coarse correction is defined on the one-step coarse propagator");
+    // mc^-a b(d + r/mc), d < P, 1 <= r <= mc, per instance (b(x) = (x+1)^{1-a} - x^{1-a}), and
+    // the substep size and mu, on the host
+    std::vector<double> w;
+    std::vector<float> wd;
+    for (int b = 0; b < h->B; ++b) {
+        InstDev& I = h->inst[b];
+        I.mc = c;
+        I.dtc = I.dT / c;
+        I.muc = std::pow(I.dtc, I.alpha) * std::tgamma(2.0 - I.alpha);
+        I.oBc = (long long)w.size();
+        const double ma = std::pow((double)c, -I.alpha);
+        for (int d = 0; d < h->P; ++d)
+            for (int r = 1; r <= c; ++r) {
+                const double x = d + (double)r / c;
+                const double bx = std::pow(x + 1.0, 1.0 - I.alpha) - std::pow(x, 1.0 - I.alpha);
+                const double v = ma * bx;
+                w.push_back(v);
+                const float hi = (float)v;
+                wd.push_back(hi);
+                wd.push_back((float)(v - (double)hi));
+            }
+    }
+    if (w.size() > h->bcc_cap) {
+        TRY(dalloc(h, &h->d_bcc, w.size()));
+        TRY(dalloc(h, &h->d_bccd, w.size()));   // float pairs in 8-byte slots
+        h->bcc_cap = w.size();
+    }
+    CU(h, cudaMemcpyAsync(h->d_bcc, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->d_bccd, wd.data(), sizeof(float) * wd.size(), cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(InstDev) * h->B, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    h->pa.bcc = h->d_bcc;
+    h->pa.bccd = reinterpret_cast<const df*>(h->d_bccd);
+    if (h->par_graph) {   // the graph holds the kernels' arguments
+        cudaGraphExecDestroy(h->par_graph);
+        h->par_graph = nullptr;
+    }
     return PSL1_OK;
 }
 
@@ -1817,6 +1896,8 @@ psl1_status psl1_set_coarse(psl1_h h, psl1_mlp_h mh)
         return PSL1_OK;
     }
     if (h->pa.dim2) return fail(h, PSL1_ERR_ARG, "the learned coarse correction is defined for 1D instances");
+    if (h->inst[0].mc > 1)
+        return fail(h, PSL1_ERR_ARG, "the learned coarse correction is defined on the one-step coarse propagator");
     for (int b = 0; b < h->B; ++b)
         if (h->inst[b].basis == PSL1_BASIS_CHEB)
             return fail(h, PSL1_ERR_ARG, "the learned coarse correction is defined for sine-basis instances");

@@ -48,6 +48,9 @@ struct InstDev {
     int basis;                   // 0 sine Galerkin, 1 Chebyshev-Lobatto collocation (Mx intervals, K = Mx - 1)
     long long oC;                // collocation: offset in the collocation pool (nodes, sines, Dm)
     float inner_rtol;            // relative residual of the FP32 inner CG in the refined mixed step
+    int mc;                      // coarse propagator substeps (1: the one-step L1 G)
+    double dtc, muc;             // substep size dT/mc and its mu
+    long long oBc;               // offset of mc^-a b(d + r/mc), d < P, r <= mc, in the substep weight pool
 };
 
 struct TabDev {

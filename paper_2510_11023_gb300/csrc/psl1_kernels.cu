@@ -301,23 +301,44 @@ __device__ __forceinline__ void check_finite(const PathArgs& a, const double* v,
         if (!isfinite(v[k])) report(a.status, -3, ii, where, info);
 }
 
-// F_n of instance ii on coarse states U (rows 0..n, global): m fine steps with
+// The grid a slice is propagated on: its steps, step size, mu and the
+// coarse-history weights m^-a b(d + r/m) (row d < P, column r - 1 < m).
+struct SliceGrid {
+    int m;
+    double dt, mu;
+    const double* bC;
+    const df* bCd;
+};
+
+// the fine grid of Eq. FineGrid (m = N/P steps per slice)
+__device__ __forceinline__ SliceGrid fine_grid(const PathArgs& a, const InstDev& I)
+{
+    return {I.m, I.dt, I.mu, a.bp + I.oB + I.Nb + 1, a.bpd + I.oB + I.Nb + 1};
+}
+
+// the coarse propagator's substep grid (mc steps per slice)
+__device__ __forceinline__ SliceGrid substep_grid(const PathArgs& a, const InstDev& I)
+{
+    return {I.mc, I.dtc, I.muc, a.bcc + I.oBc, a.bccd + I.oBc};
+}
+
+// F_n of instance ii on coarse states U (rows 0..n, global): g.m steps with
 // the local fine history kept in the CTA's ring and the coarse history
 // m^-a sum_{i=1}^n b(n-i+r/m) (U_i - U_{i-1})  (Eq. L1Fine, difference form).
 template <bool D2>
 __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, double* Vout, double* out,
-                           Carve& cv, double* ring, bool one_solve = false)
+                           Carve& cv, double* ring, bool one_solve, const SliceGrid& g)
 {
     const InstDev& I = a.inst[ii];
-    const int K = I.K, m = I.m, tid = threadIdx.x;
+    const int K = I.K, m = g.m, tid = threadIdx.x;
     const double* bF = a.bp + I.oB;
-    const double* bC = bF + I.Nb + 1;
+    const double* bC = g.bC;
     // FP32-pipe paths: the history sums accumulate in double-float, the coarse
     // differences U_i - U_{i-1} are formed once per slice, and the ring holds
     // the fine differences as double-float pairs
     const bool dfh = a.prec != 0;
     const df* bFd = a.bpd + I.oB;
-    const df* bCd = bFd + I.Nb + 1;
+    const df* bCd = g.bCd;
     df* dud = a.dud + (size_t)blockIdx.x * a.dud_stride;
     df* ringd = reinterpret_cast<df*>(ring);
     for (int k = tid; k < K; k += NT) {
@@ -363,7 +384,7 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
         }
         if (tid == 0 && a.flops) atomicAdd(a.flops + a.flop_slot, 2.0 * K * (r - 1 + n));
         __syncthreads();
-        int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n + I.dt * (r - 1), I.mu, cv.nxt, cv, one_solve);
+        int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n + g.dt * (r - 1), g.mu, cv.nxt, cv, one_solve);
         if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_FINE, n * m + r);
         check_finite(a, cv.nxt, K, ii, WHERE_FINE, n * m + r);
         for (int k = tid; k < K; k += NT) {
@@ -439,6 +460,13 @@ __device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, C
 {
     const InstDev& I = a.inst[ii];
     const int K = I.K, tid = threadIdx.x;
+    if (I.mc > 1) {
+        // G with mc L1 substeps per slice: the fine propagator on the substep grid
+        // (the CTA's ring slot holds its local history); result in cv.nxt
+        double* ring = a.ring + (size_t)blockIdx.x * a.ring_stride;
+        fine_slice<D2>(a, ii, n, U, nullptr, cv.nxt, cv, ring, false, substep_grid(a, I));
+        return;
+    }
     const double* bF = a.bp + I.oB;
     for (int k = tid; k < K; k += NT) {
         double c = U[(size_t)n * K + k], h = c;
@@ -551,7 +579,8 @@ k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nuni
         // and the fixed point are unchanged.  At k = 0 no increment exists yet.
         const bool one_solve = a.loose_above > 0.0 && n > nfirst[ii] &&
                                (nfirst[ii] == 0 || a.incr[ii] > a.loose_above);
-        fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring, one_solve);
+        fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring, one_solve,
+                       fine_grid(a, I));
     }
 }
 
@@ -643,7 +672,8 @@ k_serial_hyb(PathArgs a, const double* u0, double* Us)
     double* ring = a.ring + (size_t)blockIdx.x * a.ring_stride;
     for (int k = threadIdx.x; k < I.K; k += NT) U[k] = u0[I.oK + k];
     __syncthreads();
-    for (int n = 0; n < I.P; ++n) fine_slice<D2>(a, ii, n, U, nullptr, U + (size_t)(n + 1) * I.K, cv, ring);
+    for (int n = 0; n < I.P; ++n)
+        fine_slice<D2>(a, ii, n, U, nullptr, U + (size_t)(n + 1) * I.K, cv, ring, false, fine_grid(a, I));
 }
 
 __global__ void k_uni_init(const InstDev* inst, const double* u0, double* Wcur, double* Us)
@@ -853,7 +883,7 @@ k_one_slice(PathArgs a, int ii, int n, const double* U, double* V)
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);
     const InstDev& I = a.inst[ii];
-    fine_slice<D2>(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring);
+    fine_slice<D2>(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring, false, fine_grid(a, I));
 }
 
 template <bool D2>
@@ -942,7 +972,7 @@ k_one_slice_noalloc(PathArgs a, int ii, int n, const double* U, double* V)
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);
     const InstDev& I = a.inst[ii];
-    fine_slice<D2>(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring);
+    fine_slice<D2>(a, ii, n, U, V, V + (size_t)I.m * I.K, cv, a.ring, false, fine_grid(a, I));
 }
 
 // Device address of the fixed array on the current device.  Host code cannot

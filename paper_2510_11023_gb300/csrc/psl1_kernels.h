@@ -71,6 +71,8 @@ struct PathArgs {
     const double* incr;      // last parareal increment e_k per instance (written by the correction sweep)
     double loose_above;      // > 0: inexact F stage while e_k > loose_above (MIXED only; 0: off)
     const double* cheb;      // collocation pool (nodes, sines, derivative matrices), may be null
+    const double* bcc;       // coarse-substep weights mc^-a b(d + r/mc) (FP64), may be null
+    const df* bccd;          // the same as double-float
 };
 
 // Kc: largest collocation K of the batch (0: none)

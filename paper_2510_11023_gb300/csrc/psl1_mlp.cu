@@ -1,5 +1,6 @@
 // psl1_mlp.cu -- training and inference kernels of the learned coarse correction.
 #include "psl1_mlp.h"
+#include "psl1_tc.h"
 
 namespace psl1 {
 
@@ -73,101 +74,30 @@ cudaError_t mlp_refresh_bf16(const float* master, __nv_bfloat16* w16, __nv_bfloa
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ GEMM
-// 64x64 output tile, 16-deep k tiles staged in shared memory, 256 threads with
-// 4x4 register tiles.  B is BF16 (weights) or FP32 (activations).  Optional
-// epilogue: + bias[n]; act_out = SiLU(C).
-__device__ __forceinline__ float ldB(const __nv_bfloat16* b16, const float* b32, long long i)
+// ------------------------------------------------------------------ GEMMs
+// Every product of the network runs on the tensor cores (psl1_tc.cu,
+// launch_gemm_tc: tcgen05 kind::tf32 with the FP32 operands split into TF32
+// hi + lo parts, FP32 accumulation in tensor memory; BF16 weights are exact in
+// TF32), so the forward pass, the gradients and the training keep FP32-level
+// accuracy.  Offsets of the transposed BF16 weights [in][out] of layer l.
+static long long wT_offset(const MlpLayout& L, int l)
 {
-    return b16 ? __bfloat162float(b16[i]) : b32[i];
-}
-
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int Kd, const float* A, long long sam, long long sak,
-                                              const __nv_bfloat16* B16, const float* B32, long long sbk,
-                                              long long sbn, float* C, long long scm, long long scn, float beta,
-                                              const float* bias, float* act_out)
-{
-    __shared__ float As[16][68];
-    __shared__ float Bs[16][68];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    const bool a_mfast = (sam == 1), b_nfast = (sbn == 1);
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < Kd; k0 += 16) {
-        for (int e = tid; e < 1024; e += 256) {
-            int mm = a_mfast ? (e & 63) : (e >> 4), kk = a_mfast ? (e >> 6) : (e & 15);
-            int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < Kd) ? A[(long long)m * sam + (long long)k * sak] : 0.f;
-        }
-        for (int e = tid; e < 1024; e += 256) {
-            int nn = b_nfast ? (e & 63) : (e >> 4), kk = b_nfast ? (e >> 6) : (e & 15);
-            int n = n0 + nn, k = k0 + kk;
-            Bs[kk][nn] = (n < N && k < Kd) ? ldB(B16, B32, (long long)k * sbk + (long long)n * sbn) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                a[i] = As[kk][ty * 4 + i];
-                b[i] = Bs[kk][tx * 4 + i];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int m = m0 + ty * 4 + i;
-        if (m >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int n = n0 + tx * 4 + j;
-            if (n >= N) continue;
-            long long ci = (long long)m * scm + (long long)n * scn;
-            float v = acc[i][j];
-            if (beta != 0.f) v += beta * C[ci];
-            if (bias) v += bias[n];
-            C[ci] = v;
-            if (act_out) act_out[ci] = v / (1.0f + expf(-v));
-        }
-    }
-}
-
-static cudaError_t gemm_ep(int M, int N, int Kd, const float* A, long long sam, long long sak, const __nv_bfloat16* B16,
-                           const float* B32, long long sbk, long long sbn, float* C, long long scm, long long scn,
-                           float beta, const float* bias, float* act, cudaStream_t s)
-{
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    k_gemm<<<grid, 256, 0, s>>>(M, N, Kd, A, sam, sak, B16, B32, sbk, sbn, C, scm, scn, beta, bias, act);
-    return cudaGetLastError();
-}
-
-cudaError_t gemm_f32acc(int M, int N, int Kd, const float* A, long long sam, long long sak,
-                        const __nv_bfloat16* B16, const float* B32, long long sbk, long long sbn, float* C,
-                        long long scm, long long scn, float beta, cudaStream_t s)
-{
-    return gemm_ep(M, N, Kd, A, sam, sak, B16, B32, sbk, sbn, C, scm, scn, beta, nullptr, nullptr, s);
+    long long o = 0;
+    for (int q = 0; q < l; ++q) o += (long long)L.din[q] * L.dout[q];
+    return o;
 }
 
 // pre[l] = act[l-1] W_l^T + b_l, act[l] = SiLU(pre[l]) for l < 3; Y = pre[3].
 cudaError_t mlp_forward(const float* X0, int B, const __nv_bfloat16* w16, const float* master, const MlpLayout& L,
-                        float* const* pre, float* const* act, float* Y, cudaStream_t s)
+                        float* const* pre, float* const* act, float* Y, const MlpTc& tc, cudaStream_t s)
 {
     const float* in = X0;
     for (int l = 0; l < 4; ++l) {
         int din = L.din[l], dout = L.dout[l];
         float* out = (l < 3) ? pre[l] : Y;
-        cudaError_t e = gemm_ep(B, dout, din, in, din, 1, w16 + L.oW[l], nullptr, 1, din, out, dout, 1, 0.f,
-                                master + L.ob[l], l < 3 ? act[l] : nullptr, s);
+        // out[b][o] = sum_i in[b][i] W[o][i] + b[o]  (W rows are K-major: the flat layout)
+        cudaError_t e = launch_gemm_tc(B, dout, din, in, din, w16 + L.oW[l], nullptr, din, out, dout, 0.f,
+                                       master + L.ob[l], l < 3 ? act[l] : nullptr, tc.status, s);
         if (e != cudaSuccess) return e;
         in = (l < 3) ? act[l] : nullptr;
     }
@@ -214,7 +144,7 @@ __global__ void k_colsum(const float* D, int B, int N, float* db)
 
 cudaError_t mlp_backward(const float* X0, int B, const float* T, const __nv_bfloat16* w16, const MlpLayout& L,
                          float* const* pre, float* const* act, const float* Y, float* dY, float* dH, float* dH2,
-                         float* grad, float* loss_acc, cudaStream_t s)
+                         float* grad, float* loss_acc, const MlpTc& tc, cudaStream_t s)
 {
     const int nout = L.dout[3];
     const int n = B * nout;
@@ -226,14 +156,19 @@ cudaError_t mlp_backward(const float* X0, int B, const float* T, const __nv_bflo
     for (int l = 3; l >= 0; --l) {
         int din = L.din[l], dout = L.dout[l];
         const float* xin = (l > 0) ? act[l - 1] : X0;
-        // dW_l = d^T xin : C[o][i] = sum_b d[b][o] xin[b][i]
-        e = gemm_ep(dout, din, B, d, 1, dout, nullptr, xin, din, 1, grad + L.oW[l], din, 1, 0.f, nullptr, nullptr, s);
+        // dW_l = d^T xin : C[o][i] = sum_b d[b][o] xin[b][i], both operands transposed to K(=b)-major
+        e = launch_transpose(d, B, dout, tc.tA, s);
+        if (e == cudaSuccess) e = launch_transpose(xin, B, din, tc.tB, s);
+        if (e == cudaSuccess)
+            e = launch_gemm_tc(dout, din, B, tc.tA, B, nullptr, tc.tB, B, grad + L.oW[l], din, 0.f, nullptr, nullptr,
+                               tc.status, s);
         if (e != cudaSuccess) return e;
         k_colsum<<<(dout + 255) / 256, 256, 0, s>>>(d, B, dout, grad + L.ob[l]);
         if (l == 0) break;
-        // dX = d W_l : C[b][i] = sum_o d[b][o] W[o][i]
+        // dX = d W_l : C[b][i] = sum_o d[b][o] W[o][i] = sum_o d[b][o] W^T[i][o]
         float* dx = bufs[l & 1];
-        e = gemm_ep(B, din, dout, d, dout, 1, w16 + L.oW[l], nullptr, din, 1, dx, din, 1, 0.f, nullptr, nullptr, s);
+        e = launch_gemm_tc(B, din, dout, d, dout, tc.wT + wT_offset(L, l), nullptr, dout, dx, din, 0.f, nullptr,
+                           nullptr, tc.status, s);
         if (e != cudaSuccess) return e;
         long long nn = (long long)B * din;
         k_silu_back<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(dx, pre[l - 1], nn);

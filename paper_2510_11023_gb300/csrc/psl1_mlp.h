@@ -8,7 +8,8 @@
 //
 // Flat parameter layout (shared with the CPU oracle): W1[W][nin], b1[W],
 // W2[W][W], b2[W], W3[W][W], b3[W], W4[nout][W], b4[nout].  FP32 master
-// weights and Adam moments; BF16 copies feed every product; FP32 accumulation.
+// weights and Adam moments; BF16 copies feed every product, on the tensor
+// cores with FP32 accumulation.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -42,16 +43,20 @@ MlpLayout mlp_layout(int nin, int width, int nout);
 cudaError_t mlp_init_params(float* master, const MlpLayout& L, unsigned long long seed, cudaStream_t s);
 cudaError_t mlp_refresh_bf16(const float* master, __nv_bfloat16* w16, __nv_bfloat16* wT, float* bias,
                              const MlpLayout& L, cudaStream_t s);
-// C(m,n) = beta C(m,n) + sum_k A(m,k) B(k,n), strided operands, FP32 accumulation
-cudaError_t gemm_f32acc(int M, int N, int Kd, const float* A, long long sam, long long sak,
-                        const __nv_bfloat16* B16, const float* B32, long long sbk, long long sbn, float* C,
-                        long long scm, long long scn, float beta, cudaStream_t s);
+// what the tensor-core products of the network need besides the weights:
+// the transposed BF16 weights, two transpose buffers (>= B x max(width, nin,
+// nout) floats each) and a device status word (set if a bounded wait gave up)
+struct MlpTc {
+    const __nv_bfloat16* wT;
+    float *tA, *tB;
+    int* status;
+};
 cudaError_t mlp_forward(const float* X0, int B, const __nv_bfloat16* w16, const float* master, const MlpLayout& L,
-                        float* const* pre, float* const* act, float* Y, cudaStream_t s);
+                        float* const* pre, float* const* act, float* Y, const MlpTc& tc, cudaStream_t s);
 // loss = mean (Y - T)^2, dY = 2 (Y - T) / (B nout); gradients of every parameter
 cudaError_t mlp_backward(const float* X0, int B, const float* T, const __nv_bfloat16* w16, const MlpLayout& L,
                          float* const* pre, float* const* act, const float* Y, float* dY, float* dH, float* dH2,
-                         float* grad, float* loss_acc, cudaStream_t s);
+                         float* grad, float* loss_acc, const MlpTc& tc, cudaStream_t s);
 cudaError_t mlp_adam(float* master, const float* grad, float* m, float* v, long long n, int t, float lr, float b1,
                      float b2, float eps, cudaStream_t s);
 cudaError_t mlp_gather(const float* Z, const float* T, const int* valid, int S, int nin, int nout, int B, long long a,

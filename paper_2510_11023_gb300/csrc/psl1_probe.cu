@@ -44,7 +44,60 @@ double measure(int blocks, int threads, int iters, T* buf, cudaStream_t s)
     return best;
 }
 
+// FP64 tensor-core throughput: four independent accumulators per warp of
+// mma.sync m8n8k4 f64 (512 FLOP per instruction and warp)
+__global__ void k_dmma_chains(double* out, int iters)
+{
+    const double a = 1.0 + threadIdx.x * 1e-9, b = 1.0 - threadIdx.x * 1e-9;
+    double c[4][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                         : "+d"(c[j][0]), "+d"(c[j][1])
+                         : "d"(a), "d"(b));
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t += c[j][0] + c[j][1];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
 }  // namespace
+
+extern "C" psl1_status psl1_probe_dmma(double* fp64_tensor_tflops)
+{
+    if (!fp64_tensor_tflops) return PSL1_ERR_ARG;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PSL1_ERR_CUDA;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = nsm * 8, threads = 256, iters = 2000;
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) return PSL1_ERR_NOMEM;
+    cudaStream_t s;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, s);
+        k_dmma_chains<<<blocks, threads, 0, s>>>((double*)buf, iters);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double tf = 512.0 * 4 * blocks * (threads / 32) * (double)iters / (ms * 1e-3) / 1e12;
+        if (rep > 0 && tf > best) best = tf;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    cudaFree(buf);
+    *fp64_tensor_tflops = best;
+    return e == cudaSuccess ? PSL1_OK : PSL1_ERR_CUDA;
+}
 
 extern "C" psl1_status psl1_probe_peaks(double* fp64_tflops, double* fp32_tflops)
 {

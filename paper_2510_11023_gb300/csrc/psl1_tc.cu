@@ -281,6 +281,186 @@ __global__ void k_tc_tables(const double* Dt, const double* C, const double* wh,
         w[q] = (float)wh[q < Qh ? q : Q - 1 - q];
 }
 
+// ------------------------------------------------------------------ GEMM for the MLP
+// C[m][n] = beta C[m][n] + sum_k A[m][k] B[n][k] (+ bias[n]); act[m][n] = SiLU(C[m][n])
+// when act is given.  A (FP32) and B (BF16 weights, or FP32 data when SPLIT_B)
+// are K-major with row strides lda, ldb.  tcgen05.mma kind::tf32: every FP32
+// operand is split into TF32 parts, x = hi + lo with hi = x truncated to TF32
+// (the bits the tensor cores read) and lo = x - hi (exact in FP32), and the
+// products hi*hi + lo*hi (+ hi*lo) are accumulated in FP32 in tensor memory,
+// so the result has FP32-level accuracy (BF16 weights are exact in TF32).
+// One CTA per 128 x 128 output tile, 32 K-elements (128 bytes per row) per
+// stage in two shared-memory buffers, the same core-matrix geometry as above.
+constexpr int GN = 128;                     // output columns per CTA (tensor-memory columns)
+constexpr int GKC = 32;                     // K elements (FP32) per stage
+
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// byte offset of FP32 element (row r, k c) in a K-major 32-element stage
+__device__ __forceinline__ int tile_off4(int r, int c)
+{
+    return (r >> 3) * SBO + (c >> 2) * LBO + (r & 7) * 16 + (c & 3) * 4;
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+template <bool SPLIT_B>
+__global__ void __launch_bounds__(TNT) k_gemm_tc(int M, int N, int K, const float* __restrict__ A, long long lda,
+                                                 const __nv_bfloat16* __restrict__ B16, const float* __restrict__ B32,
+                                                 long long ldb, float* C, long long ldc, float beta,
+                                                 const float* __restrict__ bias, float* act, int* status)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.x * GN, m0 = blockIdx.y * TM;
+    constexpr int tbytes = TM * GKC * 4;              // one 128-row operand tile (16 KB)
+    constexpr int stage = (SPLIT_B ? 4 : 3) * tbytes;  // A hi, A lo, B hi [, B lo]
+    unsigned char* st[2] = {sm, sm + stage};
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * stage);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(GN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = idesc_tf32(TM, GN);
+    const int nchunks = (K + GKC - 1) / GKC;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+        const int b = c & 1;
+        if (c >= 2) ok = mbar_wait(&bar[b], (uint32_t)(((c - 2) >> 1) & 1));
+        if (!ok) break;
+        unsigned char* ah = st[b];
+        unsigned char* al = ah + tbytes;
+        unsigned char* bh = al + tbytes;
+        unsigned char* bl = bh + tbytes;
+        const int k0 = c * GKC;
+        for (int e = tid; e < TM * GKC; e += TNT) {   // A: split into TF32 hi + lo, zero outside
+            const int r = e / GKC, kk = e % GKC, m = m0 + r, k = k0 + kk;
+            const float x = (m < M && k < K) ? A[(long long)m * lda + k] : 0.f;
+            const float h = tf32_hi(x);
+            *reinterpret_cast<float*>(ah + tile_off4(r, kk)) = h;
+            *reinterpret_cast<float*>(al + tile_off4(r, kk)) = x - h;
+        }
+        for (int e = tid; e < GN * GKC; e += TNT) {   // B rows n0 + r
+            const int r = e / GKC, kk = e % GKC, n = n0 + r, k = k0 + kk;
+            float x = 0.f;
+            if (n < N && k < K) x = SPLIT_B ? B32[(long long)n * ldb + k] : __bfloat162float(B16[(long long)n * ldb + k]);
+            const float h = SPLIT_B ? tf32_hi(x) : x;
+            *reinterpret_cast<float*>(bh + tile_off4(r, kk)) = h;
+            if (SPLIT_B) *reinterpret_cast<float*>(bl + tile_off4(r, kk)) = x - h;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int kk = 0; kk < GKC / 8; ++kk) {   // K-step 8 = two K-adjacent cores of 4 FP32
+                const uint32_t off = kk * 2 * LBO;
+                const uint64_t dah = smem_desc(smem_u32(ah + off)), dal = smem_desc(smem_u32(al + off));
+                const uint64_t dbh = smem_desc(smem_u32(bh + off));
+                mma_tf32(tmem, dah, dbh, idesc, (c > 0 || kk > 0) ? 1 : 0);
+                mma_tf32(tmem, dal, dbh, idesc, 1);
+                if (SPLIT_B) mma_tf32(tmem, dah, smem_desc(smem_u32(bl + off)), idesc, 1);
+            }
+            mma_commit(&bar[b]);
+        }
+        __syncthreads();
+    }
+    if (ok && nchunks > 0) ok = mbar_wait(&bar[(nchunks - 1) & 1], (uint32_t)(((nchunks - 1) >> 1) & 1));
+    if (!ok && tid == 0) atomicCAS(status, 0, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int m = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < GN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (m < M) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int n = n0 + c0 + i;
+                    if (n >= N) continue;
+                    const long long ci = (long long)m * ldc + n;
+                    float y = v[i];
+                    if (beta != 0.f) y += beta * C[ci];
+                    if (bias) y += bias[n];
+                    C[ci] = y;
+                    if (act) act[ci] = y / (1.0f + expf(-y));
+                }
+            }
+        }
+    } else {
+        mbar_wait(&bar[0], 0);
+        mbar_wait(&bar[1], 0);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GN));
+}
+
+cudaError_t launch_gemm_tc(int M, int N, int K, const float* A, long long lda, const __nv_bfloat16* B16,
+                           const float* B32, long long ldb, float* C, long long ldc, float beta, const float* bias,
+                           float* act, int* status, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid((N + GN - 1) / GN, (M + TM - 1) / TM);
+    const bool split = B32 != nullptr;
+    const size_t sm = 2 * (size_t)(split ? 4 : 3) * TM * GKC * 4 + 64;
+    if (split) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_gemm_tc<true><<<grid, TNT, sm, s>>>(M, N, K, A, lda, B16, B32, ldb, C, ldc, beta, bias, act, status);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_gemm_tc<false><<<grid, TNT, sm, s>>>(M, N, K, A, lda, B16, B32, ldb, C, ldc, beta, bias, act, status);
+    }
+    return cudaGetLastError();
+}
+
+// out[c][r] = in[r][c] (rows x cols FP32), 32 x 32 tiles through shared memory
+__global__ void k_transpose(const float* __restrict__ in, int rows, int cols, float* __restrict__ out)
+{
+    __shared__ float t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[i][threadIdx.x] = in[(long long)r * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[(long long)c * rows + r] = t[threadIdx.x][i];
+    }
+}
+
+cudaError_t launch_transpose(const float* in, int rows, int cols, float* out, cudaStream_t s)
+{
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    k_transpose<<<grid, block, 0, s>>>(in, rows, cols, out);
+    return cudaGetLastError();
+}
+
 size_t assemble_tc_smem(int Npad) { return 2 * (size_t)(TM + Npad) * TKC * 2 + 64; }
 
 cudaError_t launch_tc_tables(const double* Dt, const double* C, const double* wh, int K, int Qh, int Kpad, int Qpad,

@@ -71,6 +71,7 @@ SIGNATURES = {
     "psl1_keep_iterates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "psl1_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "psl1_set_inexact_fine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "psl1_set_coarse_substeps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "psl1_get_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D]),
     "psl1_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "psl1_get_soe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, _D, ctypes.c_int,
@@ -84,6 +85,7 @@ SIGNATURES = {
     "psl1_fine_slice_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                ctypes.c_void_p]),
     "psl1_probe_peaks": (ctypes.c_int, [_D, _D]),
+    "psl1_probe_dmma": (ctypes.c_int, [_D]),
     "psl1_mlp_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_ulonglong, ctypes.c_void_p]),
     "psl1_mlp_nparams": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
@@ -168,6 +170,13 @@ def psl1_probe_peaks() -> tuple:
     a, b = ctypes.c_double(), ctypes.c_double()
     _chk(load().psl1_probe_peaks(ctypes.byref(a), ctypes.byref(b)), None)
     return a.value, b.value
+
+
+def psl1_probe_dmma() -> float:
+    """Measured FP64 tensor-core (DMMA) throughput of the current device, TFLOP/s."""
+    a = ctypes.c_double()
+    _chk(load().psl1_probe_dmma(ctypes.byref(a)), None)
+    return a.value
 
 
 def psl1_destroy(h) -> None:
@@ -271,8 +280,8 @@ class Problem:
         _chk(self.L.psl1_set_graph(self.h, int(on)), self.h)
 
     def set_inexact_fine(self, above: float):
-        """Inexact early iterations: one FP32 solve per fine step on slices n > k
-        while the last increment exceeds `above` (0: off).  MIXED 1D only."""
+        """Inexact early iterations: the FP32 step on slices n > k while the last
+        increment exceeds `above` (0: off).  MIXED handles (1D and 2D)."""
         _chk(self.L.psl1_set_inexact_fine(self.h, float(above)), self.h)
 
     def get_iterate(self, k: int) -> list:
@@ -309,6 +318,10 @@ class Problem:
         _chk(self.L.psl1_assemble(self.h, b, {"tensor": 0, "moments": 1}[method], units, _dp(D),
                                   A.ctypes.data_as(_F), ctypes.byref(ms)), self.h)
         return A, ms.value
+
+    def set_coarse_substeps(self, c: int):
+        """L1 substeps per slice of the coarse propagator (1: the paper's one-step G)."""
+        _chk(self.L.psl1_set_coarse_substeps(self.h, int(c)), self.h)
 
     def autotune(self, cache_path: str | None = None) -> bool:
         """Tune the F stage (see psl1_autotune); True if every choice came from the cache."""

@@ -737,3 +737,28 @@ def test_collocation_parareal_finite_termination_paper_shape():
     assert k == P
     for j in range(k + 1):
         assert np.abs(U[j][: j + 1] - S[: j + 1]).max() <= 1e-13 * np.abs(S).max(), j
+
+
+# ---------------------------------------------------------------- coarse propagator with substeps
+def test_coarse_substeps_limits_and_fixed_point():
+    # G with c L1 substeps per slice: c = 1 is the paper's G (bitwise), c = m is F itself,
+    # so the initial coarse sweep already is S_hyb and one iteration confirms it; any c keeps
+    # the exact prefix and the fixed point (Eq. PararealConvergence)
+    K, P, m = 12, 6, 4
+    kw = dict(Mx=K, N=P * m, P=P, alpha=0.45, dpar=(1, 0.5, 0, 0, 0.2), fpar=CFG1_F)
+    u0 = cfg1_u0(K)
+    S = O.serial_hyb(O.make_prob(**kw), u0)
+    U1, e1, k1 = O.parareal(O.make_prob(**kw), u0, 1e-13)
+    Uc1, ec1, kc1 = O.parareal(O.make_prob(coarse_substeps=1, **kw), u0, 1e-13)
+    assert k1 == kc1 and np.array_equal(U1, Uc1)
+    pm = O.make_prob(coarse_substeps=m, **kw)
+    assert np.abs(O.coarse_sweep(pm, u0) - S).max() < 1e-14 * np.abs(S).max()
+    Um, em, km = O.parareal(pm, u0, 1e-13)
+    assert km == 1 and np.abs(Um[-1] - S).max() < 1e-14 * np.abs(S).max()
+    U2, e2, k2 = O.parareal(O.make_prob(coarse_substeps=2, **kw), u0, 0.0)
+    for j in range(k2 + 1):
+        assert np.abs(U2[j][: j + 1] - S[: j + 1]).max() <= 1e-13 * np.abs(S).max(), j
+    # two substeps contract faster than one
+    _, ea, _ = O.parareal(O.make_prob(**kw), u0, 0.0, max_iter=3)
+    _, eb, _ = O.parareal(O.make_prob(coarse_substeps=2, **kw), u0, 0.0, max_iter=3)
+    assert eb[2] < ea[2]
