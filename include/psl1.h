@@ -174,7 +174,22 @@ psl1_status psl1_solve_serial(psl1_h h, int kind);
  * at max_iter above tol.                                                    */
 psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_out);
 
-/* Copy coefficients at the coarse nodes, sum_b (P+1) K_b doubles:
+/* Resume parareal from a checkpoint (no counterpart in the paper): U (host,
+ * sum_b (P+1) K_b doubles) is the iterate U^{k0} of an earlier solve of the
+ * same problem with the same coarse propagator after k0 iterations
+ * (psl1_get_iterate or psl1_get_coeffs), 0 <= k0 < max_iter.  G_old(n) =
+ * G_n(U^{k0}_{0:n}) is recomputed at those states -- the values the earlier
+ * solve held -- and the iteration continues at k0 with slices n >= k0, so it
+ * ends where the uninterrupted solve would (bitwise, the kernels being
+ * deterministic) for every instance still iterating at k0 (all instances
+ * are taken as active there).  Iteration counts include the k0 done before; the
+ * increment log and kept iterates start at e_{k0} and U^{k0}.  The last
+ * increment is not part of the checkpoint, so resumed F stages are refined
+ * (inexact early iterations apply only to fresh solves).  Runs the host
+ * loop (graph mode is not used).                                          */
+psl1_status psl1_resume_parareal(psl1_h h, int k0, const double* U, double tol, int max_iter, int* iters_out);
+
+/* Copy coefficients at the coarse nodes, sum_b (P+1) K_b doubles:/* Copy coefficients at the coarse nodes, sum_b (P+1) K_b doubles:
  * which = 0: the current parareal iterate, 1: the last serial solve.       */
 psl1_status psl1_get_coeffs(psl1_h h, int which, double* out);
 psl1_status psl1_get_coeffs_dev(psl1_h h, int which, double* d_out);
@@ -266,7 +281,9 @@ psl1_status psl1_assemble(psl1_h h, int b, int method, int units, const double* 
  *    fewer CG iterations and more double-float refinement sweeps); a
  *    candidate is kept only if its slice-end states agree with the
  *    default's to 1e-10 relative;
- *  - every precision: the persistent F stage's CTAs, one or two per SM.
+ *  - every precision: the persistent F stage's CTAs per SM -- one or two
+ *    with the kernel's registers bounded for two, or three with them
+ *    bounded for three (fewer registers, some spilling); 2D: one.
  * cache_path (may be NULL): a file of JSON lines {"key": ..., "value": ...}
  * keyed by device name, precision, dimension and bucket (or unit count);
  * cached choices are applied without timing, new ones are appended.

@@ -467,7 +467,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         h->Nmax = std::max(h->Nmax, I.N);
     }
     int nbmax = h->Kpmax / TILE;
-    int nslots = std::max(2 * h->nsm, batch);
+    int nslots = std::max(3 * h->nsm, batch);   // up to three F-stage CTAs per SM (autotuned)
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const bool two_d = in[0].dim == 2;
@@ -601,6 +601,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.incr = h->d_incr;
     a.loose_above = 0.0;
     a.cheb = h->d_cheb;
+    a.fstage_minb = 2;
     h->iters.assign(batch, 0);
     h->errlog.assign(batch, {});
     h->d_Ucur = h->d_Ua;
@@ -999,6 +1000,9 @@ static psl1_status solve_parareal_graph(psl1_problem* h, double tol, int maxit)
     return PSL1_OK;
 }
 
+static psl1_status parareal_host(psl1_problem* h, int k0, const double* Uk0, double tol, int maxit, int* iters_out,
+                                 std::chrono::steady_clock::time_point t0);
+
 psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_out)
 {
     if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
@@ -1016,21 +1020,41 @@ psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_o
         TRY(solve_parareal_graph(h, tol, maxit));
         return finish_parareal(h, tol, maxit, iters_out, t0);
     }
+    return parareal_host(h, -1, nullptr, tol, maxit, iters_out, t0);
+}
+
+// The host-driven iteration.  k0 < 0: start from the coarse sweep (U^0, and
+// G_old(n) = G_n(U^0_{0:n}) along it); k0 >= 0: resume from the checkpoint
+// U^{k0} (host), with G_old(n) = G_n(U^{k0}_{0:n}) recomputed at those states --
+// the values the interrupted iteration held, so the continuation is the same.
+static psl1_status parareal_host(psl1_problem* h, int k0, const double* Uk0, double tol, int maxit, int* iters_out,
+                                 std::chrono::steady_clock::time_point t0)
+{
+    const int B = h->B;
     std::vector<int> nfirst(B, 0), active(B, 1);
     std::vector<double> incr(B, 0.0);
     double* Uk = h->d_Ua;
     double* Uk1 = h->d_Ub;
     CU(h, cudaMemcpyAsync(h->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, h->stream));
-    // step 1: U^0 by the coarse sweep, G_old(n) = G_n(U^0_{0:n})
     CU(h, cudaEventRecord(h->ev[0], h->stream));
-    CU(h, launch_coarse_sweep(h->pa, B, h->d_u0, nullptr, Uk, nullptr, h->d_Gold, 1, h->d_nfirst, h->d_active,
-                              h->d_incr, h->stream));
+    if (k0 < 0) {
+        // step 1: U^0 by the coarse sweep, G_old(n) = G_n(U^0_{0:n})
+        CU(h, launch_coarse_sweep(h->pa, B, h->d_u0, nullptr, Uk, nullptr, h->d_Gold, 1, h->d_nfirst, h->d_active,
+                                  h->d_incr, h->stream));
+    } else {
+        CU(h, cudaMemcpyAsync(Uk, Uk0, sizeof(double) * h->sumU, cudaMemcpyHostToDevice, h->stream));
+        // the last increment is not part of the checkpoint: zero keeps every resumed F stage refined
+        CU(h, cudaMemsetAsync(h->d_incr, 0, sizeof(double) * B, h->stream));
+        CU(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
+        CU(h, launch_coarse_at(h->pa, Uk, h->d_Gold, h->d_units, h->nunits, h->d_counter, fstage_grid(h),
+                               h->stream));
+    }
     CU(h, cudaEventRecord(h->ev[1], h->stream));
     h->stats.kernel_launches = 1;
     TRY(check_device_status(h));
     h->stats.ms_coarse += elapsed(h->ev[0], h->ev[1]);
     if (h->keep_iterates) TRY(snapshot(h, Uk));
-    int k = 0;
+    int k = k0 < 0 ? 0 : k0;
     for (; k < maxit; ++k) {
         for (int b = 0; b < B; ++b) nfirst[b] = k;
         count_work(h, nfirst, active);
@@ -1069,6 +1093,23 @@ psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_o
     }
     h->d_Ucur = Uk;
     return finish_parareal(h, tol, maxit, iters_out, t0);
+}
+
+psl1_status psl1_resume_parareal(psl1_h h, int k0, const double* Uk0, double tol, int max_iter, int* iters_out)
+{
+    if (!h || !Uk0) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    if (!h->u0_set) return fail(h, PSL1_ERR_STATE, "set u0 before solving");
+    if (!(tol >= 0.0)) return fail(h, PSL1_ERR_ARG, "tol must be >= 0");
+    const int P = h->P;
+    int maxit = (max_iter <= 0 || max_iter > P) ? P : max_iter;
+    if (k0 < 0 || k0 >= maxit) return fail(h, PSL1_ERR_ARG, "k0 must be in [0, max_iter)");
+    auto t0 = std::chrono::steady_clock::now();
+    h->stats = psl1_stats{};
+    h->iterates.clear();
+    h->iters.assign(h->B, k0);
+    h->errlog.assign(h->B, {});
+    TRY(reset_status(h));
+    return parareal_host(h, k0, Uk0, tol, maxit, iters_out, t0);
 }
 
 psl1_status psl1_get_coeffs(psl1_h h, int which, double* out)
@@ -1246,28 +1287,37 @@ psl1_status psl1_autotune(psl1_h h, const char* cache_path, int* from_cache)
     // (2) CTAs of the persistent F stage: one or two per SM
     if (st == PSL1_OK) {
         char key[256];
-        std::snprintf(key, sizeof key, "%s|%s|%s|fstage_grid|units=%d|slots=%d", dev.c_str(), prec, dim, h->nunits,
-                      h->pa.nslots);
+        std::snprintf(key, sizeof key, "%s|%s|%s|fstage_ctas_per_sm|units=%d|K<=%d", dev.c_str(), prec, dim, h->nunits,
+                      h->Kmax);
         auto it = cache.find(key);
         if (it != cache.end()) {
-            h->fgrid = (int)it->second;
+            const int c = (int)it->second;   // 1: one CTA per SM, 2: two, 3: three (register bound 3)
+            h->fgrid = c * h->nsm;
+            h->pa.fstage_minb = (c == 3 && !h->pa.dim2) ? 3 : 2;
             ++hits;
         } else {
             ++misses;
+            // candidates: (CTAs per SM, register bound) = (1, 2), (2, 2), (3, 3); 2D runs one per SM
             std::vector<int> act(h->B, 1);
             int best = 0;
             float best_ms = 0.f;
-            for (int g : {h->nsm, 2 * h->nsm}) {
+            const int cands[3][2] = {{1, 2}, {2, 2}, {3, 3}};
+            for (int c = 0; c < (h->pa.dim2 ? 1 : 3); ++c) {
+                const int g = cands[c][0] * h->nsm;
                 if (g > h->pa.nslots) continue;
                 h->fgrid = g;
+                h->pa.fstage_minb = cands[c][1];
                 float ms = 0.f;
                 if ((st = fstage_trial(h, act, &ms, nullptr)) != PSL1_OK) break;
                 if (best == 0 || ms < best_ms) {
-                    best = g;
+                    best = c + 1;
                     best_ms = ms;
                 }
             }
-            h->fgrid = best;
+            if (best) {
+                h->fgrid = cands[best - 1][0] * h->nsm;
+                h->pa.fstage_minb = cands[best - 1][1];
+            }
             if (st == PSL1_OK) fresh.push_back({key, (double)best});
         }
     }

@@ -555,8 +555,10 @@ __global__ void __launch_bounds__(NT) k_coarse_dataset(PathArgs a, const double*
     }
 }
 
-template <bool D2>
-__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+// MINB: CTAs per SM the register allocation is bounded for (1D: 2, or 3 with
+// some spilling; the autotuner picks the faster; 2D: 1)
+template <bool D2, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
 k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nunits, int* counter,
          const int* nfirst, const int* active)
 {
@@ -581,6 +583,28 @@ k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nuni
                                (nfirst[ii] == 0 || a.incr[ii] > a.loose_above);
         fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring, one_solve,
                        fine_grid(a, I));
+    }
+}
+
+// G_old(n) = G_n(U_{0:n}) of every (instance, slice) unit at given states U (a
+// parareal iteration resumed from a checkpoint); persistent CTAs over the units
+template <bool D2>
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_coarse_at(PathArgs a, const double* Uk, double* Gold, const int2* units, int nunits, int* counter)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve<D2>(a, smem_raw);
+    __shared__ int s_u;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_u = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_u;
+        if (u >= nunits) break;
+        const int ii = units[u].x, n = units[u].y;
+        const InstDev& I = a.inst[ii];
+        coarse_step<D2>(a, ii, n, Uk + I.oU, cv);
+        for (int k = threadIdx.x; k < I.K; k += NT) Gold[I.oPK + (size_t)n * I.K + k] = cv.nxt[k];
     }
 }
 
@@ -1015,8 +1039,11 @@ cudaError_t launch_fstage(const PathArgs& a, const double* Uold, double* Fv, con
 {
     size_t sm = step_smem_bytes(a);
     if (grid > a.nslots) grid = a.nslots;
-    return LAUNCH_STEP_KERNEL(k_fstage, grid, sm, s, slot(a, 0), Uold, Fv, units, nunits, counter, nfirst,
-                              active);
+    if (a.dim2)
+        return launch_k(k_fstage<true, 1>, grid, sm, s, slot(a, 0), Uold, Fv, units, nunits, counter, nfirst, active);
+    if (a.fstage_minb == 3)
+        return launch_k(k_fstage<false, 3>, grid, sm, s, slot(a, 0), Uold, Fv, units, nunits, counter, nfirst, active);
+    return launch_k(k_fstage<false, 2>, grid, sm, s, slot(a, 0), Uold, Fv, units, nunits, counter, nfirst, active);
 }
 
 cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, const double* Uold, double* Unew,
@@ -1026,6 +1053,14 @@ cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, cons
     size_t sm = step_smem_bytes(a);
     return LAUNCH_STEP_KERNEL(k_coarse_sweep, B, sm, s, slot(a, 1), u0, Uold, Unew, Fv, Gold, init, nfirst,
                               active, incr);
+}
+
+cudaError_t launch_coarse_at(const PathArgs& a, const double* Uk, double* Gold, const int2* units, int nunits,
+                             int* counter, int grid, cudaStream_t s)
+{
+    size_t sm = step_smem_bytes(a);
+    if (grid > a.nslots) grid = a.nslots;
+    return LAUNCH_STEP_KERNEL(k_coarse_at, grid, sm, s, slot(a, 1), Uk, Gold, units, nunits, counter);
 }
 
 cudaError_t launch_serial_hyb(const PathArgs& a, int B, const double* u0, double* Us, cudaStream_t s)

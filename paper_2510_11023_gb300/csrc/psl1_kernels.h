@@ -71,6 +71,7 @@ struct PathArgs {
     const double* incr;      // last parareal increment e_k per instance (written by the correction sweep)
     double loose_above;      // > 0: inexact F stage while e_k > loose_above (MIXED only; 0: off)
     const double* cheb;      // collocation pool (nodes, sines, derivative matrices), may be null
+    int fstage_minb;         // 1D F stage: CTAs per SM its registers are bounded for (2 or 3)
     const double* bcc;       // coarse-substep weights mc^-a b(d + r/mc) (FP64), may be null
     const df* bccd;          // the same as double-float
 };
@@ -89,6 +90,9 @@ cudaError_t launch_fstage(const PathArgs& a, const double* Uold, double* Fv, con
 cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, const double* Uold, double* Unew,
                                 const double* Fv, double* Gold, int init, const int* nfirst,
                                 const int* active, double* incr, cudaStream_t s);
+// G_old(n) = G_n(U_{0:n}) for every unit at given states (resumed parareal).
+cudaError_t launch_coarse_at(const PathArgs& a, const double* Uk, double* Gold, const int2* units, int nunits,
+                             int* counter, int grid, cudaStream_t s);
 // Serial solvers.
 cudaError_t launch_serial_hyb(const PathArgs& a, int B, const double* u0, double* Us, cudaStream_t s);
 cudaError_t launch_uni_init(const PathArgs& a, int B, const double* u0, double* Wcur, double* Us,

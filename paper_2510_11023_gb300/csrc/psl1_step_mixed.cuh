@@ -250,7 +250,6 @@ __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const do
     const int tid = threadIdx.x, K = I.K, Qh = Tb.Qh;
     const df* Std = reinterpret_cast<const df*>(tp + Tb.oStd);
     const double* xh = tp + Tb.oX;
-    const double* wh = tp + Tb.oWq;
     const double* aux = tp + Tb.oAux;
     const double mid2 = I.lo0 + I.hi0;
     float* part32 = reinterpret_cast<float*>(ms.part);
@@ -291,22 +290,27 @@ __device__ void nodes_moments_mixed(const InstDev& I, const TabDev& Tb, const do
         ms.fpd[q] = df_mul(w, fs);
         ms.fmd[q] = df_mul(w, fd);
     }
+    // the FP32 step: every node quantity in FP32 (float copies of the weights and node
+    // functions); only the manufactured sources, when present, are evaluated in FP64
+    const bool src = I.fpar[4] != 0.0 || I.fpar[5] != 0.0;
     for (int q = tid; q < Qh && fp32_only; q += NT) {
-        const double o = df_to_double(ms.wpd[q]), e = df_to_double(ms.wmd[q]);
-        const double ua = o + e, ub = o - e;
-        double xa = xh[q], xb = mid2 - xa, w = wh[q];
-        const double Da = D_eval32(I, (float)aux[4 * q], (float)aux[4 * q + 1], (float)ua);
-        const double Db = D_eval32(I, (float)aux[4 * q + 2], (float)aux[4 * q + 3], (float)ub);
-        double fa = f_eval(I, xa, aux[4 * q], te, ua);   // sources keep FP64 (rarely used)
-        double fb = f_eval(I, xb, aux[4 * q + 2], te, ub);
-        if (I.fpar[4] == 0.0 && I.fpar[5] == 0.0) {
-            fa = f_eval32(I, (float)aux[4 * q], (float)te, (float)ua);
-            fb = f_eval32(I, (float)aux[4 * q + 2], (float)te, (float)ub);
+        const float o = ms.wpd[q].hi, e = ms.wmd[q].hi;   // FP32 transform outputs (lo = 0)
+        const float ua = o + e, ub = o - e, w = wd[q].hi;
+        const float sa1 = auxd[4 * q].hi, sa2 = auxd[4 * q + 1].hi, sb1 = auxd[4 * q + 2].hi, sb2 = auxd[4 * q + 3].hi;
+        const float Da = D_eval32(I, sa1, sa2, ua), Db = D_eval32(I, sb1, sb2, ub);
+        float fa, fb;
+        if (src) {
+            const double xa = xh[q], xb = mid2 - xa;
+            fa = (float)f_eval(I, xa, aux[4 * q], te, (double)ua);
+            fb = (float)f_eval(I, xb, aux[4 * q + 2], te, (double)ub);
+        } else {
+            fa = f_eval32(I, sa1, (float)te, ua);
+            fb = f_eval32(I, sb1, (float)te, ub);
         }
-        ms.wpd[q] = df_from_double(w * (Da + Db));
-        ms.wmd[q] = df_from_double(w * (Da - Db));
-        ms.fpd[q] = df_from_double(w * (fa + fb));
-        ms.fmd[q] = df_from_double(w * (fa - fb));
+        ms.wpd[q] = df{w * (Da + Db), 0.f};
+        ms.wmd[q] = df{w * (Da - Db), 0.f};
+        ms.fpd[q] = df{w * (fa + fb), 0.f};
+        ms.fmd[q] = df{w * (fa - fb), 0.f};
     }
     __syncthreads();
     // moments g_s (even s: w (D_q + D_q'), odd s: w (D_q - D_q')) and the load (even k: f_q + f_q')

@@ -64,6 +64,7 @@ SIGNATURES = {
     "psl1_set_u0_dev": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "psl1_solve_serial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "psl1_solve_parareal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, _I]),
+    "psl1_resume_parareal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_double, ctypes.c_int, _I]),
     "psl1_get_coeffs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D]),
     "psl1_get_coeffs_dev": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "psl1_get_iterations": (ctypes.c_int, [ctypes.c_void_p, _I]),
@@ -244,6 +245,19 @@ class Problem:
     def solve_parareal(self, tol: float = 1e-10, max_iter: int = 0, allow_not_converged: bool = False) -> int:
         it = ctypes.c_int(0)
         st = self.L.psl1_solve_parareal(self.h, float(tol), int(max_iter), ctypes.byref(it))
+        if st == -6 and allow_not_converged:
+            return it.value
+        _chk(st, self.h)
+        return it.value
+
+    def resume_parareal(self, k0: int, U, tol: float = 1e-10, max_iter: int = 0,
+                        allow_not_converged: bool = False) -> int:
+        """Continue parareal from the checkpoint U^{k0} (a list of (P+1) x K arrays or the flat vector)."""
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(u).reshape(-1) for u in U])
+                                    if isinstance(U, (list, tuple)) else U, dtype=np.float64)
+        assert flat.size == self.offU[-1]
+        it = ctypes.c_int(0)
+        st = self.L.psl1_resume_parareal(self.h, int(k0), _dp(flat), float(tol), int(max_iter), ctypes.byref(it))
         if st == -6 and allow_not_converged:
             return it.value
         _chk(st, self.h)

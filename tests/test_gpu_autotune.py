@@ -30,7 +30,7 @@ def test_autotune_writes_and_reuses_cache(tmp_path):
         assert first[b]["inner_rtol"] in (np.float32(1e-7), np.float32(1e-5), np.float32(3e-4))
     lines = [json.loads(l) for l in open(cache)]
     keys = [l["key"] for l in lines]
-    assert any("fstage_grid" in k for k in keys) and any("inner_rtol" in k for k in keys)
+    assert any("fstage_ctas_per_sm" in k for k in keys) and any("inner_rtol" in k for k in keys)
     with psl1.Problem(wl, precision="mixed") as pr:
         assert pr.autotune(cache) is True
         assert [pr.tuning(b) for b in range(wl.B)] == first
