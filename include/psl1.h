@@ -189,7 +189,7 @@ psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_o
  * loop (graph mode is not used).                                          */
 psl1_status psl1_resume_parareal(psl1_h h, int k0, const double* U, double tol, int max_iter, int* iters_out);
 
-/* Copy coefficients at the coarse nodes, sum_b (P+1) K_b doubles:/* Copy coefficients at the coarse nodes, sum_b (P+1) K_b doubles:
+/* Copy coefficients at the coarse nodes, sum_b (P+1) K_b doubles:
  * which = 0: the current parareal iterate, 1: the last serial solve.       */
 psl1_status psl1_get_coeffs(psl1_h h, int which, double* out);
 psl1_status psl1_get_coeffs_dev(psl1_h h, int which, double* d_out);
@@ -223,15 +223,21 @@ psl1_status psl1_set_graph(psl1_h h, int on);
  * step of PSL1_PREC_FP32 (FP32 transforms, D and f, one FP32 inner solve)
  * instead of the refined step, as long as the instance's last increment
  * e_{k-1} exceeds `above` (and always at k = 0); slice n = k, which starts
- * from exact states, keeps the refined step.  The fixed point (the
- * sequential F sweep S_hyb) and the exactness of U^{k+1}_{0:k+1} are
- * unchanged; the cheaper early F stages perturb the iterate by about the
- * FP32 step's error (~1e-6 relative), which the later, refined
- * iterations remove, so `above` should stay well above that (1e-4 is used by
- * the benchmark).  Affects MIXED instances (1D and 2D); a no-op for FP64 and
- * FP32.  Rebuilds the parareal graph.  PSL1_ERR_ARG for negative or
- * non-finite values.  No counterpart in the paper (an implementation choice:
- * its iteration, Eq. Parareal, uses the same F throughout).                 */
+ * from exact states, keeps the refined step.  In the same iterations (and
+ * in the initial coarse sweep) the coarse propagator G is evaluated with
+ * the FP32 step as well.  When an instance's mode changes, its stored
+ * values G_n(U^k_{0:n}), n >= k, are first recomputed in the new mode (one
+ * parallel launch), so each iteration uses one G at both call sites of
+ * Eq. Parareal.  The fixed point (the sequential F sweep S_hyb) and the
+ * exactness of U^{k+1}_{0:k+1} are unchanged; the cheaper early iterations
+ * perturb the iterate by about the FP32 step's error (~1e-6 relative),
+ * which the later, refined iterations remove, so `above` should stay well
+ * above that (the benchmark tries 1e-4 and 1e-5).  Affects MIXED instances
+ * (1D and 2D); a no-op for FP64 and FP32.  psl1_solve_serial's coarse
+ * solution always uses the refined G.  Rebuilds the parareal graph.
+ * PSL1_ERR_ARG for negative or non-finite values.  No counterpart in the
+ * paper (an implementation choice: its iteration, Eq. Parareal, uses the
+ * same F and G throughout).                                                 */
 psl1_status psl1_set_inexact_fine(psl1_h h, double above);
 
 /* Coarse propagator with c L1 substeps per slice (1 <= c <= the smallest m
@@ -247,7 +253,7 @@ psl1_status psl1_set_inexact_fine(psl1_h h, double above);
  * the one-step G).  Rebuilds the parareal graph.                           */
 psl1_status psl1_set_coarse_substeps(psl1_h h, int c);
 
-/* Statistics of the last solve.                                             *//* Statistics of the last solve.                                             */
+/* Statistics of the last solve.                                             */
 psl1_status psl1_get_stats(psl1_h h, psl1_stats* st);
 
 /* Dense stiffness matrices of the 1D sine-basis instance b (Eq. AForm with
@@ -293,7 +299,7 @@ psl1_status psl1_autotune(psl1_h h, const char* cache_path, int* from_cache);
 /* The tuned inner tolerance of instance b and the F stage's CTA count.      */
 psl1_status psl1_get_tuning(psl1_h h, int b, float* inner_rtol, int* fstage_ctas);
 
-/* Exponents s and weights w (cap entries each, may be NULL) of the fast/* Exponents s and weights w (cap entries each, may be NULL) of the fast/* Exponents s and weights w (cap entries each, may be NULL) of the fast
+/* Exponents s and weights w (cap entries each, may be NULL) of the fast
  * history of instance b: b(x) ~ sum_i w_i exp(-s_i x) for 16 <= x <= N_b;
  * len receives their number (0 for alpha = 1, which has no history).       */
 psl1_status psl1_get_soe(psl1_h h, int b, double* s, double* w, int cap, int* len);

@@ -59,6 +59,7 @@ struct psl1_problem {
     double *d_Ua = nullptr, *d_Ub = nullptr, *d_Us = nullptr, *d_Fv = nullptr, *d_Gold = nullptr;
     double *d_incr = nullptr, *d_work = nullptr, *d_ring = nullptr;
     int *d_nfirst = nullptr, *d_active = nullptr, *d_counter = nullptr;
+    int* d_gmode = nullptr;   // per instance: the stored G_old values are FP32-step values
     int2* d_units = nullptr;
     int nunits = 0;
     DevStatus* d_status = nullptr;
@@ -499,6 +500,12 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     CTRY(dalloc(h, &h->d_nfirst, batch));
     CTRY(dalloc(h, &h->d_active, batch));
     CTRY(dalloc(h, &h->d_counter, 1));
+    CTRY(dalloc(h, &h->d_gmode, batch));
+    if (cudaMemset(h->d_gmode, 0, sizeof(int) * batch) != cudaSuccess) {
+        g_create_error = "cudaMemset failed";
+        psl1_destroy(h);
+        return PSL1_ERR_CUDA;
+    }
     CTRY(dalloc(h, &h->d_status, 1));
     CTRY(dalloc(h, &h->d_flops, 4));
     if (!cheb_pool.empty()) CTRY(dalloc(h, &h->d_cheb, cheb_pool.size()));
@@ -600,6 +607,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.L2 = lay2;
     a.incr = h->d_incr;
     a.loose_above = 0.0;
+    a.gmode = h->d_gmode;
     a.cheb = h->d_cheb;
     a.fstage_minb = 2;
     h->iters.assign(batch, 0);
@@ -811,7 +819,9 @@ psl1_status psl1_solve_serial(psl1_h h, int kind)
             h->stats.fine_step_modes += (double)h->inst[b].N * h->inst[b].K;
         }
     } else if (kind == PSL1_SERIAL_COARSE) {
-        CU(h, launch_coarse_sweep(h->pa, h->B, h->d_u0, nullptr, h->d_Us, nullptr, h->d_Gold, 1, h->d_nfirst,
+        PathArgs exact = h->pa;   // the coarse solution itself: never the inexact G
+        exact.loose_above = 0.0;
+        CU(h, launch_coarse_sweep(exact, h->B, h->d_u0, nullptr, h->d_Us, nullptr, h->d_Gold, 1, h->d_nfirst,
                                   h->d_active, h->d_incr, h->stream));
         h->stats.kernel_launches = 1;
     } else if (kind == PSL1_SERIAL_UNIFORM) {
@@ -899,7 +909,8 @@ psl1_status psl1_set_graph(psl1_h h, int on)
 }
 
 // The graph-mode iteration: a while node whose body is
-//   F stage (U^k -> F_old), correction sweep (U^k -> U^{k+1}, e_k), U^k <- U^{k+1},
+//   F stage (U^k -> F_old), [inexact iterations: G_old brought into this
+//   iteration's coarse-step mode], correction sweep (U^k -> U^{k+1}, e_k), U^k <- U^{k+1},
 //   update (log e_k, retire converged instances, k += 1, loop condition).
 // CTAs of the persistent F stage: the tuned count, at most one per workspace slot
 static int fstage_grid(const psl1_problem* h)
@@ -936,6 +947,9 @@ static psl1_status build_parareal_graph(psl1_problem* h)
             const int grid = fstage_grid(h);
             cudaError_t q = launch_fstage(h->pa, h->d_Ua, h->d_Fv, h->d_units, h->nunits, h->d_counter, h->d_nfirst,
                                           h->d_active, grid, h->stream);
+            if (q == cudaSuccess && h->pa.loose_above > 0.0)
+                q = launch_coarse_regold(h->pa, h->d_Ua, h->d_Gold, h->d_units, h->nunits, h->d_nfirst, h->d_active,
+                                         grid, h->stream);
             if (q == cudaSuccess)
                 q = launch_coarse_sweep(h->pa, h->B, h->d_u0, h->d_Ua, h->d_Ub, h->d_Fv, h->d_Gold, 0, h->d_nfirst,
                                         h->d_active, h->d_incr, h->stream);
@@ -995,7 +1009,7 @@ static psl1_status solve_parareal_graph(psl1_problem* h, double tol, int maxit)
         }
         count_work(h, nfirst, active);
     }
-    h->stats.kernel_launches = 1 + 3 * itmax;
+    h->stats.kernel_launches = 1 + (h->pa.loose_above > 0.0 ? 4 : 3) * itmax;
     h->d_Ucur = h->d_Ua;
     return PSL1_OK;
 }
@@ -1048,6 +1062,7 @@ static psl1_status parareal_host(psl1_problem* h, int k0, const double* Uk0, dou
         CU(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
         CU(h, launch_coarse_at(h->pa, Uk, h->d_Gold, h->d_units, h->nunits, h->d_counter, fstage_grid(h),
                                h->stream));
+        CU(h, cudaMemsetAsync(h->d_gmode, 0, sizeof(int) * B, h->stream));   // G_old: refined values
     }
     CU(h, cudaEventRecord(h->ev[1], h->stream));
     h->stats.kernel_launches = 1;
@@ -1066,6 +1081,11 @@ static psl1_status parareal_host(psl1_problem* h, int k0, const double* Uk0, dou
         CU(h, launch_fstage(h->pa, Uk, h->d_Fv, h->d_units, h->nunits, h->d_counter, h->d_nfirst, h->d_active,
                             grid, h->stream));
         CU(h, cudaEventRecord(h->ev[1], h->stream));
+        if (h->pa.loose_above > 0.0) {
+            CU(h, launch_coarse_regold(h->pa, Uk, h->d_Gold, h->d_units, h->nunits, h->d_nfirst, h->d_active, grid,
+                                       h->stream));
+            h->stats.kernel_launches += 1;
+        }
         CU(h, launch_coarse_sweep(h->pa, B, h->d_u0, Uk, Uk1, h->d_Fv, h->d_Gold, 0, h->d_nfirst, h->d_active,
                                   h->d_incr, h->stream));
         CU(h, cudaEventRecord(h->ev[2], h->stream));
@@ -1774,6 +1794,7 @@ psl1_status psl1_mlp_dataset(psl1_mlp_h mh, psl1_h data, int source, int iters)
     MCU(mh, cudaMemsetAsync(mh->R, 0, sizeof(float) * (size_t)S * mh->nout, mh->stream));
     MCU(mh, cudaMemsetAsync(data->d_status, 0, sizeof(DevStatus), mh->stream));
     PathArgs run = data->pa;          // the data problem's own coarse propagator
+    run.loose_above = 0.0;            // samples from refined F and G only
     PathArgs feat = data->pa;         // feature / sample layout of this network
     feat.mlp = mh->dev();
     std::vector<int> valid;

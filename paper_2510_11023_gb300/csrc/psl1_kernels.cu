@@ -455,8 +455,9 @@ __device__ void learned_correction(const PathArgs& a, const InstDev& I, int n, C
 
 // G_n of instance ii on U (rows 0..n, global) -> cv.nxt.  History in the
 // difference form U_n - sum_{j=0}^{n-1} b_{n-j} (U_{j+1} - U_j) of Eq. L1Scheme.
+// one_solve: the FP32 step (inexact early iterations; MIXED handles).
 template <bool D2>
-__device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, Carve& cv)
+__device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, Carve& cv, bool one_solve = false)
 {
     const InstDev& I = a.inst[ii];
     const int K = I.K, tid = threadIdx.x;
@@ -464,7 +465,7 @@ __device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, C
         // G with mc L1 substeps per slice: the fine propagator on the substep grid
         // (the CTA's ring slot holds its local history); result in cv.nxt
         double* ring = a.ring + (size_t)blockIdx.x * a.ring_stride;
-        fine_slice<D2>(a, ii, n, U, nullptr, cv.nxt, cv, ring, false, substep_grid(a, I));
+        fine_slice<D2>(a, ii, n, U, nullptr, cv.nxt, cv, ring, one_solve, substep_grid(a, I));
         return;
     }
     const double* bF = a.bp + I.oB;
@@ -476,7 +477,7 @@ __device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, C
     }
     if (tid == 0 && a.flops) atomicAdd(a.flops + a.flop_slot, 2.0 * K * n);
     __syncthreads();
-    int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n, I.muT, cv.nxt, cv);
+    int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n, I.muT, cv.nxt, cv, one_solve);
     if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_COARSE, n);
     check_finite(a, cv.nxt, K, ii, WHERE_COARSE, n);
     if constexpr (!D2)   // the learned correction is defined for 1D instances
@@ -555,6 +556,15 @@ __global__ void __launch_bounds__(NT) k_coarse_dataset(PathArgs a, const double*
     }
 }
 
+// Inexact early iterations (opt-in, MIXED handles: prec 1): while an instance's last increment
+// is above a.loose_above (and in its first iteration, k = nfirst = 0, when no
+// increment exists yet), its F stage runs the slices n > nfirst with the FP32
+// step and its coarse sweep evaluates G with the FP32 step.
+__device__ __forceinline__ bool inexact_iteration(const PathArgs& a, int ii, int nfirst)
+{
+    return a.prec == 1 && a.loose_above > 0.0 && (nfirst == 0 || a.incr[ii] > a.loose_above);
+}
+
 // MINB: CTAs per SM the register allocation is bounded for (1D: 2, or 3 with
 // some spilling; the autotuner picks the faster; 2D: 1)
 template <bool D2, int MINB>
@@ -575,12 +585,10 @@ k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nuni
         const int ii = units[u].x, n = units[u].y;
         if (!active[ii] || n < nfirst[ii]) continue;
         const InstDev& I = a.inst[ii];
-        // Inexact early iterations (opt-in): while the last increment is large, the
-        // slices after the first one still in error take one FP32 solve per step.
-        // Slice n = nfirst starts from exact states and stays exact, so U^{k+1}_{k+1}
-        // and the fixed point are unchanged.  At k = 0 no increment exists yet.
-        const bool one_solve = a.loose_above > 0.0 && n > nfirst[ii] &&
-                               (nfirst[ii] == 0 || a.incr[ii] > a.loose_above);
+        // Inexact early iterations: the slices after the first one still in error
+        // take the FP32 step.  Slice n = nfirst starts from exact states and stays
+        // exact, so U^{k+1}_{k+1} and the fixed point are unchanged.
+        const bool one_solve = n > nfirst[ii] && inexact_iteration(a, ii, nfirst[ii]);
         fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring, one_solve,
                        fine_grid(a, I));
     }
@@ -608,6 +616,32 @@ k_coarse_at(PathArgs a, const double* Uk, double* Gold, const int2* units, int n
     }
 }
 
+// G_old(n), n >= nfirst, recomputed in the coarse-step mode of this iteration for
+// every active instance whose stored values were taken in the other mode (the
+// iteration switches between the FP32 and the refined G).  Each iteration of
+// Eq. Parareal then uses one G at both of its call sites, G_n(U^{k+1}_{0:n})
+// and G_n(U^k_{0:n}); the convergence result holds for any G, so the fixed
+// point is the same.  Grid-stride over the units: iterations without a switch
+// (nearly all) only read the flags.
+template <bool D2>
+__global__ void __launch_bounds__(NT, D2 ? 1 : 2)
+k_coarse_regold(PathArgs a, const double* Uk, double* Gold, const int2* units, int nunits, const int* nfirst,
+                const int* active)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Carve cv = carve<D2>(a, smem_raw);
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const int ii = units[u].x, n = units[u].y;
+        if (!active[ii] || n < nfirst[ii]) continue;
+        const bool want = inexact_iteration(a, ii, nfirst[ii]);
+        if ((a.gmode[ii] != 0) == want) continue;
+        const InstDev& I = a.inst[ii];
+        coarse_step<D2>(a, ii, n, Uk + I.oU, cv, want);
+        for (int k = threadIdx.x; k < I.K; k += NT) Gold[I.oPK + (size_t)n * I.K + k] = cv.nxt[k];
+        __syncthreads();
+    }
+}
+
 template <bool D2>
 __global__ void __launch_bounds__(NT, D2 ? 1 : 2)
 k_coarse_sweep(PathArgs a, const double* u0, const double* Uold, double* Unew, const double* Fv, double* Gold,
@@ -632,11 +666,15 @@ k_coarse_sweep(PathArgs a, const double* u0, const double* Uold, double* Unew, c
         n0 = nfirst[ii];
         for (int e = tid; e < (n0 + 1) * K; e += NT) U[e] = Uold[I.oU + e];
     }
+    // the coarse-step mode of this sweep; G_old is stored in it (k_coarse_regold
+    // has brought the values this sweep reads into the same mode)
+    const bool g32 = inexact_iteration(a, ii, n0);
+    if (tid == 0 && a.gmode) a.gmode[ii] = g32;
     __syncthreads();
     double* Go = Gold + I.oPK;
     const double* Fo = Fv + I.oPK;
     for (int n = n0; n < P; ++n) {
-        coarse_step<D2>(a, ii, n, U, cv);
+        coarse_step<D2>(a, ii, n, U, cv, g32);
         for (int k = tid; k < K; k += NT) {
             double g = cv.nxt[k];
             size_t e = (size_t)n * K + k;
@@ -1061,6 +1099,15 @@ cudaError_t launch_coarse_at(const PathArgs& a, const double* Uk, double* Gold, 
     size_t sm = step_smem_bytes(a);
     if (grid > a.nslots) grid = a.nslots;
     return LAUNCH_STEP_KERNEL(k_coarse_at, grid, sm, s, slot(a, 1), Uk, Gold, units, nunits, counter);
+}
+
+cudaError_t launch_coarse_regold(const PathArgs& a, const double* Uk, double* Gold, const int2* units, int nunits,
+                                 const int* nfirst, const int* active, int grid, cudaStream_t s)
+{
+    if (!a.gmode) return cudaErrorInvalidValue;
+    size_t sm = step_smem_bytes(a);
+    if (grid > a.nslots) grid = a.nslots;
+    return LAUNCH_STEP_KERNEL(k_coarse_regold, grid, sm, s, slot(a, 1), Uk, Gold, units, nunits, nfirst, active);
 }
 
 cudaError_t launch_serial_hyb(const PathArgs& a, int B, const double* u0, double* Us, cudaStream_t s)

@@ -74,6 +74,7 @@ struct PathArgs {
     int fstage_minb;         // 1D F stage: CTAs per SM its registers are bounded for (2 or 3)
     const double* bcc;       // coarse-substep weights mc^-a b(d + r/mc) (FP64), may be null
     const df* bccd;          // the same as double-float
+    int* gmode;              // per instance: 1 if the stored G_old values are FP32-step values
 };
 
 // Kc: largest collocation K of the batch (0: none)
@@ -93,6 +94,10 @@ cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, cons
 // G_old(n) = G_n(U_{0:n}) for every unit at given states (resumed parareal).
 cudaError_t launch_coarse_at(const PathArgs& a, const double* Uk, double* Gold, const int2* units, int nunits,
                              int* counter, int grid, cudaStream_t s);
+// Inexact early iterations: G_old(n), n >= nfirst, of every active instance whose
+// coarse-step mode changes at this iteration, recomputed in the new mode.
+cudaError_t launch_coarse_regold(const PathArgs& a, const double* Uk, double* Gold, const int2* units, int nunits,
+                                 const int* nfirst, const int* active, int grid, cudaStream_t s);
 // Serial solvers.
 cudaError_t launch_serial_hyb(const PathArgs& a, int B, const double* u0, double* Us, cudaStream_t s);
 cudaError_t launch_uni_init(const PathArgs& a, int B, const double* u0, double* Wcur, double* Us,

@@ -2,12 +2,16 @@
 
 While an instance's last increment is above the threshold, the F stage of
 iteration k runs slices n > k with one FP32 inner solve per fine step; slice
-n = k starts from exact states and keeps the refined solve.  Parareal's
+n = k starts from exact states and keeps the refined solve.  The coarse sweep
+of those iterations evaluates G with the FP32 step too, and G_old is
+recomputed in the refined mode when an instance switches.  Parareal's
 properties must survive (Eq. PararealConvergence): after k iterations the
 states U^k_{0:k} equal the sequential F sweep S_hyb, the iteration still ends
-at S_hyb, and graph mode reproduces the host loop bitwise.  Tolerances are
-those of the mixed path: 1e-13 relative for the exact prefix (as in the
-finite-termination test of the refined path), 1e-10 for whole solves."""
+at S_hyb, graph mode reproduces the host loop bitwise, and the first refined
+iteration is exactly one refined iteration from its starting iterate.
+Tolerances are those of the mixed path: 1e-13 relative for the exact prefix
+(as in the finite-termination test of the refined path), 1e-10 for whole
+solves."""
 import numpy as np
 import pytest
 
@@ -111,3 +115,44 @@ def test_inexact_2d_exact_prefix_and_fixed_point():
         U = pr.get_coeffs("parareal")
     for b in range(wl.B):
         assert rel(U[b], S[b]) < TOL_SOLVE, b
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_switch_to_refined_iteration_recomputes_stored_coarse_values(dim):
+    # From the first refined iteration k_s of an instance on, the iteration must be
+    # Eq. Parareal with the refined G at both call sites.  A resumed solve from
+    # U^{k_s} computes G_old = G_n(U^{k_s}_{0:n}) afresh in the refined mode, so one
+    # resumed iteration reproduces U^{k_s+1} bitwise only if the switch brought the
+    # stored FP32-step values into the refined mode.
+    wl = _batch() if dim == 1 else workloads.small_batch_2d()
+    tau = 1e-4
+    with psl1.Problem(wl, precision="mixed") as pr:
+        pr.set_inexact_fine(tau)
+        pr.keep_iterates(True)
+        pr.solve_parareal(tol=1e-12)
+        its = pr.get_iterations()
+        logs = [pr.get_errlog(b) for b in range(wl.B)]
+        iters = [pr.get_iterate(k) for k in range(int(max(its)) + 1)]
+    switch = {}
+    for b in range(wl.B):
+        ks = next((k for k in range(1, int(its[b])) if logs[b][k - 1] <= tau), None)
+        if ks is not None:
+            switch.setdefault(ks, []).append(b)
+    assert switch, "no instance reached a refined iteration before converging"
+    for ks, bs in sorted(switch.items()):
+        with psl1.Problem(wl, precision="mixed") as pr:
+            pr.resume_parareal(ks, iters[ks], tol=0.0, max_iter=ks + 1, allow_not_converged=True)
+            U = pr.get_coeffs("parareal")
+        for b in bs:
+            assert np.array_equal(U[b], iters[ks + 1][b]), (ks, b)
+
+
+def test_serial_coarse_solution_ignores_the_inexact_setting():
+    wl = _batch()
+    with psl1.Problem(wl, precision="mixed") as pr:
+        pr.solve_serial("coarse")
+        C0 = pr.get_coeffs("serial", flat=True)
+        pr.set_inexact_fine(1e-4)
+        pr.solve_serial("coarse")
+        C1 = pr.get_coeffs("serial", flat=True)
+    assert np.array_equal(C0, C1)
