@@ -288,8 +288,9 @@ psl1_status psl1_assemble(psl1_h h, int b, int method, int units, const double* 
  *    candidate is kept only if its slice-end states agree with the
  *    default's to 1e-10 relative;
  *  - every precision: the persistent F stage's CTAs per SM -- one or two
- *    with the kernel's registers bounded for two, or three with them
- *    bounded for three (fewer registers, some spilling); 2D: one.
+ *    with the kernel's registers bounded for two, or three or four with
+ *    them bounded for three or four (fewer registers, some spilling); 2D:
+ *    one.
  * cache_path (may be NULL): a file of JSON lines {"key": ..., "value": ...}
  * keyed by device name, precision, dimension and bucket (or unit count);
  * cached choices are applied without timing, new ones are appended.

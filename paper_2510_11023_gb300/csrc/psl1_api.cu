@@ -468,7 +468,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
         h->Nmax = std::max(h->Nmax, I.N);
     }
     int nbmax = h->Kpmax / TILE;
-    int nslots = std::max(3 * h->nsm, batch);   // up to three F-stage CTAs per SM (autotuned)
+    int nslots = std::max(4 * h->nsm, batch);   // up to four F-stage CTAs per SM (autotuned)
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const bool two_d = in[0].dim == 2;
@@ -477,6 +477,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     if (two_d) {
         lay2 = make_layout2d(precision, h->Kmax, nT2, nN2, ntab2, max_smem - 1024);
         lay.total = lay2.smem;
+        lay.fine = lay2.smem;
     } else {
         lay = make_layout(precision, h->Kmax, h->Kpmax, h->Qhmax, Kc);
     }
@@ -1304,25 +1305,27 @@ psl1_status psl1_autotune(psl1_h h, const char* cache_path, int* from_cache)
             fresh.push_back({key, (double)best});
         }
     }
-    // (2) CTAs of the persistent F stage: one or two per SM
+    // (2) CTAs of the persistent F stage: one to four per SM
     if (st == PSL1_OK) {
         char key[256];
         std::snprintf(key, sizeof key, "%s|%s|%s|fstage_ctas_per_sm|units=%d|K<=%d", dev.c_str(), prec, dim, h->nunits,
                       h->Kmax);
         auto it = cache.find(key);
         if (it != cache.end()) {
-            const int c = (int)it->second;   // 1: one CTA per SM, 2: two, 3: three (register bound 3)
+            const int c = (int)it->second;   // CTAs per SM; 3 and 4 run the variants bounded for them
             h->fgrid = c * h->nsm;
-            h->pa.fstage_minb = (c == 3 && !h->pa.dim2) ? 3 : 2;
+            h->pa.fstage_minb = (c >= 3 && !h->pa.dim2) ? c : 2;
             ++hits;
         } else {
             ++misses;
-            // candidates: (CTAs per SM, register bound) = (1, 2), (2, 2), (3, 3); 2D runs one per SM
+            // candidates: (CTAs per SM, register bound) = (1, 2), (2, 2), (3, 3), (4, 4); 2D runs one
+            // per SM.  A candidate whose CTAs do not all fit at once still runs correctly (the
+            // queue is persistent, no CTA waits on another) and loses on time.
             std::vector<int> act(h->B, 1);
             int best = 0;
             float best_ms = 0.f;
-            const int cands[3][2] = {{1, 2}, {2, 2}, {3, 3}};
-            for (int c = 0; c < (h->pa.dim2 ? 1 : 3); ++c) {
+            const int cands[4][2] = {{1, 2}, {2, 2}, {3, 3}, {4, 4}};
+            for (int c = 0; c < (h->pa.dim2 ? 1 : 4); ++c) {
                 const int g = cands[c][0] * h->nsm;
                 if (g > h->pa.nslots) continue;
                 h->fgrid = g;

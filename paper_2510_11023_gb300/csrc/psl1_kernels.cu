@@ -163,14 +163,11 @@ SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int Kc)
     L.cgq = pcg ? take(4 * (size_t)Kpmax) : -1;
     L.cgpl = pcg ? take(4 * (size_t)Kpmax) : -1;
     L.cgdinv = pcg ? take(4 * (size_t)Kpmax) : -1;
-    L.cgred = pcg ? take(4 * 2 * (NT / 32)) : -1;
+    L.cgred = pcg ? take(4 * 4 * (NT / 32)) : -1;
     L.cggs = pcg ? take(4 * (size_t)(2 * Kmax + 8)) : -1;
     L.cggh = pcg ? take(4 * (size_t)(2 * Kmax + 8)) : -1;
     L.cgpart = pcg ? take(4 * (size_t)(4 * NT)) : -1;
     L.mpart = f64 ? -1 : take(8 * 2 * (size_t)NT);
-    L.mz = take(8 * (size_t)MLP_MAX_IN);
-    L.mh0 = take(8 * (size_t)MLP_MAX_WIDTH);
-    L.mh1 = take(8 * (size_t)MLP_MAX_WIDTH);
     const bool ch = Kc > 0;   // collocation: dense K x K system, nodal vectors of n + 1 = K + 2
     L.cm = ch ? take(8 * (size_t)Kc * Kc) : -1;
     L.cu = ch ? take(8 * (size_t)(Kc + 2)) : -1;
@@ -178,11 +175,19 @@ SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int Kc)
     L.cr = ch ? take(8 * (size_t)Kc) : -1;
     L.cl = ch ? take(8 * (size_t)Kc) : -1;
     L.cpiv = ch ? take(16) : -1;
+    // the learned correction's buffers come last, so that kernels which never run it
+    // (the F stage, the serial fine sweep) launch with less shared memory: at K = 256 the
+    // F stage then fits four CTAs per SM
+    L.fine = off;
+    L.mz = take(8 * (size_t)MLP_MAX_IN);
+    L.mh0 = take(8 * (size_t)MLP_MAX_WIDTH);
+    L.mh1 = take(8 * (size_t)MLP_MAX_WIDTH);
     L.total = off;
     return L;
 }
 
 size_t step_smem_bytes(const PathArgs& a) { return (size_t)a.L.total; }
+size_t fine_smem_bytes(const PathArgs& a) { return (size_t)(a.dim2 ? a.L.total : a.L.fine); }
 
 Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long ntab, int max_smem)
 {
@@ -565,8 +570,8 @@ __device__ __forceinline__ bool inexact_iteration(const PathArgs& a, int ii, int
     return a.prec == 1 && a.loose_above > 0.0 && (nfirst == 0 || a.incr[ii] > a.loose_above);
 }
 
-// MINB: CTAs per SM the register allocation is bounded for (1D: 2, or 3 with
-// some spilling; the autotuner picks the faster; 2D: 1)
+// MINB: CTAs per SM the register allocation is bounded for (1D: 2, or 3 or 4
+// with some spilling; the autotuner picks the fastest; 2D: 1)
 template <bool D2, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nunits, int* counter,
@@ -1075,10 +1080,12 @@ cudaError_t launch_one_slice_noalloc(const PathArgs& a, double* scratch, int b, 
 cudaError_t launch_fstage(const PathArgs& a, const double* Uold, double* Fv, const int2* units, int nunits,
                           int* counter, const int* nfirst, const int* active, int grid, cudaStream_t s)
 {
-    size_t sm = step_smem_bytes(a);
+    size_t sm = fine_smem_bytes(a);
     if (grid > a.nslots) grid = a.nslots;
     if (a.dim2)
         return launch_k(k_fstage<true, 1>, grid, sm, s, slot(a, 0), Uold, Fv, units, nunits, counter, nfirst, active);
+    if (a.fstage_minb == 4)
+        return launch_k(k_fstage<false, 4>, grid, sm, s, slot(a, 0), Uold, Fv, units, nunits, counter, nfirst, active);
     if (a.fstage_minb == 3)
         return launch_k(k_fstage<false, 3>, grid, sm, s, slot(a, 0), Uold, Fv, units, nunits, counter, nfirst, active);
     return launch_k(k_fstage<false, 2>, grid, sm, s, slot(a, 0), Uold, Fv, units, nunits, counter, nfirst, active);
@@ -1112,7 +1119,7 @@ cudaError_t launch_coarse_regold(const PathArgs& a, const double* Uk, double* Go
 
 cudaError_t launch_serial_hyb(const PathArgs& a, int B, const double* u0, double* Us, cudaStream_t s)
 {
-    size_t sm = step_smem_bytes(a);
+    size_t sm = fine_smem_bytes(a);
     return LAUNCH_STEP_KERNEL(k_serial_hyb, B, sm, s, slot(a, 2), u0, Us);
 }
 

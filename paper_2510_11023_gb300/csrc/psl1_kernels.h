@@ -23,8 +23,9 @@ struct SmemLayout {
     int cdf, wpd, wmd, fpd, fmd, gdf, ydf, x, rhs, z, red;   // FP32-pipe path
     int cgx, cgr, cgp, cgq, cgpl, cgdinv, cgred, cggs, cggh, cgpart;   // PCG inner solver
     int mpart;                                                   // split-transform partial sums
-    int mz, mh0, mh1;                                            // learned correction inference
     int cm, cu, cdc, cr, cl, cpiv;                               // collocation step (FP64)
+    int mz, mh0, mh1;                                            // learned correction inference (last)
+    int fine;    // bytes used by kernels that never run the learned correction (everything before mz)
     int total;
 };
 
@@ -71,7 +72,7 @@ struct PathArgs {
     const double* incr;      // last parareal increment e_k per instance (written by the correction sweep)
     double loose_above;      // > 0: inexact F stage while e_k > loose_above (MIXED only; 0: off)
     const double* cheb;      // collocation pool (nodes, sines, derivative matrices), may be null
-    int fstage_minb;         // 1D F stage: CTAs per SM its registers are bounded for (2 or 3)
+    int fstage_minb;         // 1D F stage: CTAs per SM its registers are bounded for (2, 3 or 4)
     const double* bcc;       // coarse-substep weights mc^-a b(d + r/mc) (FP64), may be null
     const df* bccd;          // the same as double-float
     int* gmode;              // per instance: 1 if the stored G_old values are FP32-step values
@@ -81,6 +82,8 @@ struct PathArgs {
 SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int Kc = 0);
 
 size_t step_smem_bytes(const PathArgs& a);
+// the F stage and the serial fine sweep: the layout without the learned-correction buffers
+size_t fine_smem_bytes(const PathArgs& a);
 
 cudaError_t launch_tables(const TableJob& job, cudaStream_t s);
 cudaError_t launch_weights(InstDev* inst, int B, double* bpool, double* bpool_df, cudaStream_t s);

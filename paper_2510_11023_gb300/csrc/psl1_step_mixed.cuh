@@ -348,16 +348,19 @@ constexpr float REFINE_EST = 1e-13f;
 
 struct PcgSmem {
     float *x, *r, *p, *q, *pl, *dinv;   // Kp each
-    float* red2;                         // 2 * NT/32
+    float* red2;                         // 2 x (2 * NT/32): two reduction buffers, used in turn
     float *gs, *gh;                      // 2 Kmax + 8 each: moment windows
     float* part;                         // 4 NT: partial sums of the blocked product
 };
 
-// acc_k = sum_l (g_|k-l| + g_{k+l+2}) pl_l  ->  cg.q[k], k < K.
-// Each thread owns four consecutive outputs and a chunk of the columns l; the
-// Toeplitz and Hankel windows slide through registers (one new shared-memory
-// load each per column instead of eight), and the chunks are summed at the end.
-__device__ void th_product32(int K, PcgSmem& cg)
+// q_k = p_k + sc (k+1) acc_k with acc_k = sum_l (g_|k-l| + g_{k+l+2}) pl_l,
+// k < K, into cg.q; returns this thread's share of p.q (threads own the k of
+// the loop k = tid, tid + NT, ...).  Each thread first computes four
+// consecutive acc_k over a chunk of the columns l: the Toeplitz and Hankel
+// windows slide through registers (one new shared-memory load each per column
+// instead of eight); the chunks are summed after one barrier.  No barrier
+// follows: the caller's reduction publishes q.
+__device__ float th_product32(int K, float sc, PcgSmem& cg)
 {
     const int ng = (K + 3) / 4;
     int S = NT / ng;
@@ -399,31 +402,40 @@ __device__ void th_product32(int K, PcgSmem& cg)
         out[3] = a3;
     }
     __syncthreads();
+    float pq = 0.f;
     for (int k = t; k < K; k += NT) {
         float s = 0.f;
         for (int c = 0; c < S; ++c) s += cg.part[c * (4 * ng) + k];
-        cg.q[k] = s;
+        const float q = cg.p[k] + sc * (float)(k + 1) * s;
+        cg.q[k] = q;
+        pq += cg.p[k] * q;
     }
-    __syncthreads();
+    return pq;
 }
 
-__device__ __forceinline__ float2 block_sum2(float a, float b, float* red2)
+// Block sums of a and b with one barrier: the partial sums of consecutive calls
+// go to the two halves of red2 in turn (buf toggles), so a call never
+// overwrites the half that threads may still be reading from the call before;
+// the barrier of the call in between orders them.  Every thread gets the same
+// sums (same order of addition).
+__device__ __forceinline__ float2 block_sum2(float a, float b, float* red2, int& buf)
 {
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
     }
-    __syncthreads();
+    float* r = red2 + buf * (2 * (NT / 32));
+    buf ^= 1;
     if ((threadIdx.x & 31) == 0) {
-        red2[threadIdx.x >> 5] = a;
-        red2[NT / 32 + (threadIdx.x >> 5)] = b;
+        r[threadIdx.x >> 5] = a;
+        r[NT / 32 + (threadIdx.x >> 5)] = b;
     }
     __syncthreads();
     float sa = 0.f, sb = 0.f;
 #pragma unroll
     for (int w = 0; w < NT / 32; ++w) {
-        sa += red2[w];
-        sb += red2[NT / 32 + w];
+        sa += r[w];
+        sb += r[NT / 32 + w];
     }
     return make_float2(sa, sb);
 }
@@ -452,6 +464,9 @@ __device__ void pcg32(const InstDev& I, double mu, MixSmem& ms, PcgSmem& cg, int
         cg.gs[j] = j <= 2 * K ? g[d].hi : 0.f;
         cg.gh[j] = j <= 2 * K ? g[j].hi : 0.f;
     }
+    // the reductions below alternate between the two halves of red2 (the
+    // barriers of block_max above order this call's first one after any earlier use)
+    int buf = 0;
     float rz = 0.f, rr = 0.f;
     for (int k = tid; k < K; k += NT) {
         float d = 1.0f + sc * (float)((k + 1) * (k + 1)) * (g[0].hi + g[2 * k + 2].hi);
@@ -465,20 +480,14 @@ __device__ void pcg32(const InstDev& I, double mu, MixSmem& ms, PcgSmem& cg, int
         rz += r * z;
         rr += r * r;
     }
-    float2 s0 = block_sum2(rz, rr, cg.red2);
+    float2 s0 = block_sum2(rz, rr, cg.red2, buf);   // its barrier also publishes the windows and p
     rz = s0.x;
     const float stop = rtol * rtol * s0.y;
     for (int it = 0; it < maxit && s0.y > 0.f; ++it) {
         if (tid == 0) ms.flag[1] += 1;
-        // q = M p, and p.q
-        th_product32(K, cg);
-        float pq = 0.f;
-        for (int k = tid; k < K; k += NT) {
-            float q = cg.p[k] + sc * (float)(k + 1) * cg.q[k];
-            cg.q[k] = q;
-            pq += cg.p[k] * q;
-        }
-        float2 s1 = block_sum2(pq, 0.f, cg.red2);
+        // q = M p, and p.q (this reduction's barrier also publishes q)
+        const float pq = th_product32(K, sc, cg);
+        float2 s1 = block_sum2(pq, 0.f, cg.red2, buf);
         if (!(s1.x > 0.f)) {   // M p . p <= 0: not SPD (D <= 0 somewhere)
             if (tid == 0 && *ms.flag < 0) *ms.flag = 0;
             break;
@@ -494,7 +503,7 @@ __device__ void pcg32(const InstDev& I, double mu, MixSmem& ms, PcgSmem& cg, int
             rzn += r * z;
             rrn += r * r;
         }
-        float2 s2 = block_sum2(rzn, rrn, cg.red2);
+        float2 s2 = block_sum2(rzn, rrn, cg.red2, buf);
         if (s2.y <= stop) break;
         float beta = rz > 0.f ? s2.x / rz : 0.f;
         rz = s2.x;
