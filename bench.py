@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--inexact", default="auto", choices=["auto", "on", "off"],
                     help="inexact early iterations (the FP32 step on slices not yet exact while the increment "
                          "exceeds a threshold, 1e-4 or 1e-5; mixed); auto: the fastest to rel err 1e-8 in warm-up")
+    ap.add_argument("--sweep-split", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="2D: CTAs of the cluster that shares each coarse-sweep step (0: the library's choice)")
     ap.add_argument("--train-batch", type=int, default=128, help="instances the learned correction trains on")
     ap.add_argument("--train-iters", type=int, default=8)
     ap.add_argument("--train-epochs", type=int, default=40)
@@ -330,6 +332,41 @@ def alg_flops_step_1d(K: int, Q: int) -> float:
     return 4.0 * Q * K + 2.0 * Q * (2 * K + 1) + K**3 / 3.0 + 2.0 * K * K
 
 
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_fstage_dram_traffic_batched1d_256inst.md")
+
+
+def source_digest() -> str:
+    """sha256 over the library's CUDA sources and the public header: a DRAM-traffic
+    figure taken by ncu is reported only while these are unchanged."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2510_11023_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                   glob.glob(os.path.join(csrc, "*.h"))) + [os.path.join(ROOT, "include", "psl1.h")]
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic(config_key: str):
+    """DRAM bytes (read + write) per k_fstage launch from the committed ncu summary, when
+    it was captured on the current sources and on this configuration; else None."""
+    try:
+        fields = {}
+        for line in open(TRAFFIC_SUMMARY):
+            if line.startswith("- ") and ": " in line:
+                k, v = line[2:].strip().split(": ", 1)
+                fields[k.strip("`")] = v.strip().strip("`")
+        if fields.get("sources_sha256") != source_digest() or fields.get("config") != config_key:
+            return None
+        return float(fields["bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def fstage_alg_flops(wl, iters) -> tuple:
     """(algorithmic FLOPs of all F-stage launches of a solve, launches): at
     iteration k every instance still iterating runs its slices n = k..P-1."""
@@ -555,6 +592,8 @@ def main():
     ref.close()
 
     pr = psl1.Problem(wl, precision=args.precision, stream=stream.cuda_stream)
+    if dim2:
+        pr.set_sweep_split(args.sweep_split)
     if args.precision != "fp64":
         e0.record(stream)
         pr.solve_serial("hybrid")
@@ -746,8 +785,10 @@ def main():
         achieved = alg / max(fine_launches, 1) / (fine_avg_ms * 1e-3) / 1e12
         count = ("4QK + 2Q(2K+1) + K^3/3 + 2K^2 per fine step (transforms, Toeplitz+Hankel moments, "
                  "direct-solve count) x the fine steps of each launch")
+    traffic_key = f"{args.workload}|B={wl.B}|{args.precision}|{coarse}|inexact={inexact:g}"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "frac_impl": achieved_impl / peak, "traffic": None, "kernel": "k_fstage",
+            "frac_impl": achieved_impl / peak, "traffic": captured_traffic(traffic_key),
+            "traffic_config": traffic_key, "kernel": "k_fstage",
             "launches": fine_launches, "ms_per_launch": fine_avg_ms,
             "share_of_solve": {"k_fstage": fine_ms / max(solve_ms_events, 1e-9),
                                "k_coarse_sweep": coarse_ms / max(solve_ms_events, 1e-9)},
@@ -779,6 +820,7 @@ def main():
             "rel_err_vs_serial_fp64": err, "stop_tol": tol, "iterations": iters_all,
             "tuned_tolerance": tuned, "autotune": tune_info,
             "coarse_propagator": coarse, "inexact_early_iterations": {"above": inexact},
+            "sweep_split_ctas": pr.sweep_split(),
             "configurations_tried": cands, "learned_training": train_info,
             "serial_fp64_ms": serial_fp64_ms, "serial_ms": serial_ms, "serial_uniform": uniform,
             "speedup_vs_serial_fp64": serial_fp64_ms / ms_step, "speedup_vs_serial_same_precision": serial_ms / ms_step,

@@ -181,8 +181,9 @@ psl1_status psl1_solve_parareal(psl1_h h, double tol, int max_iter, int* iters_o
  * G_n(U^{k0}_{0:n}) is recomputed at those states -- the values the earlier
  * solve held -- and the iteration continues at k0 with slices n >= k0, so it
  * ends where the uninterrupted solve would (bitwise, the kernels being
- * deterministic) for every instance still iterating at k0 (all instances
- * are taken as active there).  Iteration counts include the k0 done before; the
+ * deterministic; to rounding when a 2D sweep is split across a cluster,
+ * whose G_old values come from another summation order) for every instance
+ * still iterating at k0 (all instances are taken as active there).  Iteration counts include the k0 done before; the
  * increment log and kept iterates start at e_{k0} and U^{k0}.  The last
  * increment is not part of the checkpoint, so resumed F stages are refined
  * (inexact early iterations apply only to fresh solves).  Runs the host
@@ -252,6 +253,24 @@ psl1_status psl1_set_inexact_fine(psl1_h h, double above);
  * (ii)).  Rejected while a learned correction is attached (it is defined on
  * the one-step G).  Rebuilds the parareal graph.                           */
 psl1_status psl1_set_coarse_substeps(psl1_h h, int c);
+
+/* 2D: the coarse sweep shares each coarse step among the CTAs of a
+ * thread-block cluster (no counterpart in the paper; its sweep is one
+ * sequential chain per instance).  With ctas > 1 every instance's sweep runs
+ * on a cluster of that many CTAs: each CTA owns ~1/ctas of the y node
+ * columns (the node values, D and f there, and their share of every
+ * node-to-mode transform), the partial sums are added up through distributed
+ * shared memory, and the mode-space vectors and CG iterations are carried
+ * redundantly (identical in every CTA).  Results agree with the one-CTA sweep
+ * to the rounding of the changed summation order.  ctas: 1, 2, 4 or 8; 0
+ * (the default) chooses the largest of 8, 4, 2 for which the batch's
+ * clusters fit on the SMs at once.  PSL1_ERR_ARG for other values, for 1D
+ * handles with ctas > 1, or when the configuration cannot run (shared
+ * memory, workspace, or no cluster of that size fits); the previous setting
+ * stays then.  Rebuilds the parareal graph when it changes.
+ * psl1_get_sweep_split returns the cluster size in use (1: none).          */
+psl1_status psl1_set_sweep_split(psl1_h h, int ctas);
+psl1_status psl1_get_sweep_split(psl1_h h, int* ctas);
 
 /* Statistics of the last solve.                                             */
 psl1_status psl1_get_stats(psl1_h h, psl1_stats* st);

@@ -48,6 +48,7 @@ struct psl1_problem {
     std::vector<TabDev> tabs;
     std::string err;
     int nsm = 0;
+    int max_smem = 0;        // opt-in shared memory per CTA
     // sizes
     long long sumK = 0, sumU = 0, sumPK = 0, sumB = 0, sumNK = 0, tabElems = 0;
     int Kmax = 0, Kpmax = 0, Qhmax = 0, mmax = 0, Nmax = 0;
@@ -57,7 +58,7 @@ struct psl1_problem {
     TabDev* d_tab = nullptr;
     double *d_tp = nullptr, *d_bp = nullptr, *d_bpd = nullptr, *d_dud = nullptr, *d_u0 = nullptr;
     double *d_Ua = nullptr, *d_Ub = nullptr, *d_Us = nullptr, *d_Fv = nullptr, *d_Gold = nullptr;
-    double *d_incr = nullptr, *d_work = nullptr, *d_ring = nullptr;
+    double *d_incr = nullptr, *d_work = nullptr, *d_ring = nullptr, *d_corr = nullptr;
     int *d_nfirst = nullptr, *d_active = nullptr, *d_counter = nullptr;
     int* d_gmode = nullptr;   // per instance: the stored G_old values are FP32-step values
     int2* d_units = nullptr;
@@ -286,6 +287,49 @@ static psl1_status validate(const psl1_instance& d, int P, int b)
     return PSL1_OK;
 }
 
+// 2D: the layout of one CTA of a cluster of `split` CTAs that shares each coarse-sweep
+// step (each CTA holds the node columns of ceil(Qhy / split) y pairs)
+static Layout2D split_layout(const psl1_problem* h, int split)
+{
+    long long nT = 0, nN = 0, ntab = 0;
+    for (const InstDev& I : h->inst) {
+        const long long nq = (I.Qhy + split - 1) / split;
+        nT = std::max(nT, (long long)I.Mx * (2 * nq + 1));
+        nN = std::max(nN, (long long)I.Q * 2 * nq);
+        ntab = std::max(ntab, (long long)I.Mx * I.Qh + (long long)I.My * I.Qhy);
+    }
+    return make_layout2d(h->prec, h->Kmax, nT, nN, ntab, h->max_smem - 1024, split);
+}
+
+// Use clusters of `split` CTAs for the 2D coarse sweep, if that configuration can run
+// (its arrays fit the slot workspace, B split CTAs have slots, and the device can
+// hold at least one such cluster); otherwise one CTA per instance.  Returns whether
+// the requested setting was applied.
+static bool apply_split(psl1_problem* h, int split)
+{
+    h->pa.split2d = 1;
+    if (!h->pa.dim2 || split < 2) return split <= 1;
+    const Layout2D L = split_layout(h, split);
+    if (L.smem > h->max_smem - 1024 || L.gbytes > 8 * h->pa.work_stride || (long long)h->B * split > h->pa.nslots)
+        return false;
+    PathArgs t = h->pa;
+    t.L2s = L;
+    if (coarse_sweep_clusters(t, split) < 1) return false;
+    h->pa.L2s = L;
+    h->pa.split2d = split;
+    return true;
+}
+
+// the automatic choice: the largest power of two <= 8 that leaves every instance's
+// cluster room on the SMs (none once the batch alone fills them)
+static void auto_split(psl1_problem* h)
+{
+    h->pa.split2d = 1;
+    if (!h->pa.dim2) return;
+    for (int c = 8; c >= 2; c /= 2)
+        if ((long long)h->B * c <= h->nsm && apply_split(h, c)) return;
+}
+
 psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, int precision, void* stream)
 {
     if (!out) return fail(nullptr, PSL1_ERR_ARG, "out is NULL");
@@ -471,6 +515,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     int nslots = std::max(4 * h->nsm, batch);   // up to four F-stage CTAs per SM (autotuned)
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    h->max_smem = max_smem;
     const bool two_d = in[0].dim == 2;
     SmemLayout lay{};
     Layout2D lay2{};
@@ -511,12 +556,15 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     CTRY(dalloc(h, &h->d_flops, 4));
     if (!cheb_pool.empty()) CTRY(dalloc(h, &h->d_cheb, cheb_pool.size()));
     // per-slot workspace: the FP64 1D factor, or the 2D working arrays that do not fit in shared memory
-    long long work_stride = two_d ? std::max(1LL, (lay2.gbytes + 255) / 256 * 32)   // 256-byte aligned slots
+    long long gb2 = lay2.gbytes;   // 2D: also room for the arrays of a cluster-split sweep CTA
+    for (int c = 2; two_d && c <= 8; c *= 2) gb2 = std::max(gb2, split_layout(h, c).gbytes);
+    long long work_stride = two_d ? std::max(1LL, (gb2 + 255) / 256 * 32)   // 256-byte aligned slots
                             : precision == PSL1_PREC_FP64 ? bp_elems(nbmax, TILE)
                             : 1;
     long long ring_stride = (long long)h->mmax * h->Kmax;
     CTRY(dalloc(h, &h->d_work, (size_t)nslots * work_stride));
     CTRY(dalloc(h, &h->d_ring, (size_t)nslots * ring_stride));
+    CTRY(dalloc(h, &h->d_corr, (size_t)nslots * h->Kmax));
     // mixed-path coarse differences (double-float, 8 bytes per entry)
     long long dud_stride = precision == PSL1_PREC_FP64 ? 0 : (long long)P * h->Kmax;
     if (dud_stride) CTRY(dalloc(h, &h->d_dud, (size_t)nslots * dud_stride));
@@ -595,6 +643,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.work_stride = work_stride;
     a.ring = h->d_ring;
     a.ring_stride = ring_stride;
+    a.corr = h->d_corr;
     a.nslots = nslots;
     a.Kmax = h->Kmax;
     a.Kpmax = h->Kpmax;
@@ -611,6 +660,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.gmode = h->d_gmode;
     a.cheb = h->d_cheb;
     a.fstage_minb = 2;
+    a.split2d = 1;
+    auto_split(h);
     h->iters.assign(batch, 0);
     h->errlog.assign(batch, {});
     h->d_Ucur = h->d_Ua;
@@ -1896,6 +1947,33 @@ psl1_status psl1_mlp_train(psl1_mlp_h mh, psl1_h data, int epochs, int batch, fl
     }
     MCU(mh, cudaStreamSynchronize(mh->stream));
     return check_tc(mh);
+}
+
+psl1_status psl1_set_sweep_split(psl1_h h, int ctas)
+{
+    if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
+    if (ctas != 0 && ctas != 1 && ctas != 2 && ctas != 4 && ctas != 8)
+        return fail(h, PSL1_ERR_ARG, "cluster size must be 0 (automatic), 1, 2, 4 or 8");
+    if (ctas > 1 && !h->pa.dim2) return fail(h, PSL1_ERR_ARG, "the split sweep is defined for 2D instances");
+    const int before = h->pa.split2d;
+    if (ctas == 0) {
+        auto_split(h);
+    } else if (!apply_split(h, ctas)) {
+        apply_split(h, before);
+        return fail(h, PSL1_ERR_ARG, "clusters of %d CTAs cannot run this batch's coarse sweep", ctas);
+    }
+    if (h->par_graph && h->pa.split2d != before) {   // the graph holds the launch configuration
+        cudaGraphExecDestroy(h->par_graph);
+        h->par_graph = nullptr;
+    }
+    return PSL1_OK;
+}
+
+psl1_status psl1_get_sweep_split(psl1_h h, int* ctas)
+{
+    if (!h || !ctas) return fail(h, PSL1_ERR_ARG, "NULL argument");
+    *ctas = h->pa.split2d;
+    return PSL1_OK;
 }
 
 psl1_status psl1_set_coarse_substeps(psl1_h h, int c)

@@ -25,6 +25,7 @@ struct Carve {
     PcgSmem cg;
     df *mz, *mh0, *mh1;      // learned-correction features and hidden activations (double-float)
     Step2D s2;               // 2D working arrays
+    Split sp;                // 2D: this CTA's share of a cluster-split step (size 1: the whole step)
     ChebSmem ch;             // collocation step
 };
 
@@ -66,6 +67,11 @@ __device__ __forceinline__ Carve carve2d(const PathArgs& a, char* base)
     c.s2.z = static_cast<float*>(at2(R2_Z));
     c.s2.tab32 = static_cast<float*>(at2(R2_TAB32));
     c.s2.red = at2(R2_RED);
+    if (L.off[R2_SPLIT] >= 0) {   // rank and size are set by the kernel that splits the step
+        c.sp.nred = static_cast<int*>(at2(R2_SPLIT));
+        c.sp.pb = reinterpret_cast<double*>(static_cast<char*>(at2(R2_SPLIT)) + 16);
+        c.sp.stride = a.Kmax;
+    }
     return c;
 }
 
@@ -189,7 +195,7 @@ SmemLayout make_layout(int prec, int Kmax, int Kpmax, int Qhmax, int Kc)
 size_t step_smem_bytes(const PathArgs& a) { return (size_t)a.L.total; }
 size_t fine_smem_bytes(const PathArgs& a) { return (size_t)(a.dim2 ? a.L.total : a.L.fine); }
 
-Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long ntab, int max_smem)
+Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long ntab, int max_smem, int split)
 {
     Layout2D L;
     const bool f64 = prec == 0;
@@ -197,6 +203,7 @@ Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long
     long long bytes[R2_COUNT];
     bytes[R2_BAD] = 16;
     bytes[R2_RED] = 8 * 2 * (NT / 32);
+    bytes[R2_SPLIT] = split > 1 ? 16 + 8LL * 2 * Kmax : 0;   // all-reduction counter + two partial buffers
     bytes[R2_DINV] = e * Kmax;
     bytes[R2_PX] = e * Kmax;
     bytes[R2_PR] = e * Kmax;
@@ -223,8 +230,8 @@ Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long
         L.glob[r] = 0;
         if (bytes[r] <= 0) continue;
         const long long b = (bytes[r] + 15) / 16 * 16;
-        // the flag and reduction words always sit in shared memory
-        if (soff + b <= max_smem || r == R2_BAD || r == R2_RED) {
+        // the flag and reduction words and the cluster's partial sums always sit in shared memory
+        if (soff + b <= max_smem || r == R2_BAD || r == R2_RED || r == R2_SPLIT) {
             L.off[r] = (int)soff;
             soff += b;
         } else {
@@ -254,14 +261,15 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
     if constexpr (D2) {
         const TabDev& TY = a.tab[I.tabY];
         if (a.prec == 0)
-            bad = step2d_fp64(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad);
+            bad = step2d_fp64(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad, cv.sp);
         else
-            bad = step2d_mixed(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad, a.prec == 2 || one_solve);
+            bad = step2d_mixed(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad, a.prec == 2 || one_solve,
+                               cv.sp);
         // algorithmic FLOPs: each operator application is four folded one-axis
         // transforms, 4 (Mx My Qy/2 + Mx Qy Qx/2) multiply-adds; the set-up
         // (node values, load, diagonal) costs one application, the coefficient
         // evaluation ~30 per node.
-        if (threadIdx.x == 0 && a.flops) {
+        if (threadIdx.x == 0 && a.flops && cv.sp.rank == 0) {   // once per (split) step
             const double ap = 8.0 * ((double)I.Mx * I.My * I.Qhy + (double)I.Mx * I.Qy * I.Qh);
             const double f = ap * (1.0 + cv.s.bad[1] + cv.s.bad[2]) + 30.0 * I.Q * I.Qy;
             atomicAdd(a.flops + a.flop_slot, f);
@@ -387,7 +395,7 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
                 h -= bc[(size_t)(n - i) * m] * (U[(size_t)i * K + k] - U[(size_t)(i - 1) * K + k]);
             cv.hist[k] = h;
         }
-        if (tid == 0 && a.flops) atomicAdd(a.flops + a.flop_slot, 2.0 * K * (r - 1 + n));
+        if (tid == 0 && a.flops && cv.sp.rank == 0) atomicAdd(a.flops + a.flop_slot, 2.0 * K * (r - 1 + n));
         __syncthreads();
         int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n + g.dt * (r - 1), g.mu, cv.nxt, cv, one_solve);
         if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_FINE, n * m + r);
@@ -480,7 +488,7 @@ __device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, C
         cv.cur[k] = c;
         cv.hist[k] = h;
     }
-    if (tid == 0 && a.flops) atomicAdd(a.flops + a.flop_slot, 2.0 * K * n);
+    if (tid == 0 && a.flops && cv.sp.rank == 0) atomicAdd(a.flops + a.flop_slot, 2.0 * K * n);
     __syncthreads();
     int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n, I.muT, cv.nxt, cv, one_solve);
     if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_COARSE, n);
@@ -647,6 +655,9 @@ k_coarse_regold(PathArgs a, const double* Uk, double* Gold, const int2* units, i
     }
 }
 
+// One CTA per instance; 2D with a.split2d > 1: one cluster of a.split2d CTAs
+// per instance, which share every step (Split) and run everything else
+// redundantly -- each writes the same values to U, G_old and the increment.
 template <bool D2>
 __global__ void __launch_bounds__(NT, D2 ? 1 : 2)
 k_coarse_sweep(PathArgs a, const double* u0, const double* Uold, double* Unew, const double* Fv, double* Gold,
@@ -656,7 +667,16 @@ k_coarse_sweep(PathArgs a, const double* u0, const double* Uold, double* Unew, c
     Carve cv = carve<D2>(a, smem_raw);
     __shared__ double red[NT / 32];
     __shared__ double s_num, s_den;
-    const int ii = blockIdx.x, tid = threadIdx.x;
+    const int csize = (D2 && a.split2d > 1) ? a.split2d : 1;
+    const int ii = blockIdx.x / csize, tid = threadIdx.x;
+    if (csize > 1) {
+        cv.sp.size = csize;
+        cv.sp.rank = (int)cooperative_groups::this_cluster().block_rank();
+        if (tid == 0) *cv.sp.nred = 0;
+        // every CTA of the cluster is running (and has set its counter) before any
+        // reads another's shared memory
+        cooperative_groups::this_cluster().sync();
+    }
     const InstDev& I = a.inst[ii];
     const int K = I.K, P = I.P;
     double* U = Unew + I.oU;
@@ -678,17 +698,27 @@ k_coarse_sweep(PathArgs a, const double* u0, const double* Uold, double* Unew, c
     __syncthreads();
     double* Go = Gold + I.oPK;
     const double* Fo = Fv + I.oPK;
+    // the correction F_old(n) - G_old(n) is read before the coarse step and G_old(n)
+    // written after it: in a cluster-split sweep every CTA writes G_old(n), and the
+    // cluster barriers inside the step order all reads of the old value before any
+    // write of the new one (each thread keeps its own k, so no block barrier is needed)
+    double* corr = a.corr + (size_t)blockIdx.x * a.Kmax;
     for (int n = n0; n < P; ++n) {
+        if (!init)
+            for (int k = tid; k < K; k += NT) corr[k] = Fo[(size_t)n * K + k] - Go[(size_t)n * K + k];
         coarse_step<D2>(a, ii, n, U, cv, g32);
         for (int k = tid; k < K; k += NT) {
             double g = cv.nxt[k];
             size_t e = (size_t)n * K + k;
-            U[(size_t)(n + 1) * K + k] = init ? g : g + (Fo[e] - Go[e]);
+            U[(size_t)(n + 1) * K + k] = init ? g : g + corr[k];
             Go[e] = g;
         }
         __syncthreads();
     }
-    if (init) return;
+    if (init) {
+        if (csize > 1) cooperative_groups::this_cluster().sync();   // see the end of the kernel
+        return;
+    }
     // e_k = max_n ||U^{k+1}_n - U^k_n|| / max_n ||U^{k+1}_n||
     if (tid == 0) {
         s_num = 0.0;
@@ -725,6 +755,8 @@ k_coarse_sweep(PathArgs a, const double* u0, const double* Uold, double* Unew, c
     }
     __syncthreads();
     if (tid == 0) incr[ii] = s_den > 0.0 ? s_num / s_den : s_num;
+    // no CTA leaves while another may still read its shared memory
+    if (csize > 1) cooperative_groups::this_cluster().sync();
 }
 
 template <bool D2>
@@ -1091,10 +1123,55 @@ cudaError_t launch_fstage(const PathArgs& a, const double* Uold, double* Fv, con
     return launch_k(k_fstage<false, 2>, grid, sm, s, slot(a, 0), Uold, Fv, units, nunits, counter, nfirst, active);
 }
 
+// launch configuration of the cluster-split 2D sweep (B clusters of `split` CTAs)
+static cudaLaunchConfig_t split_config(const PathArgs& a, int B, int split, cudaStream_t s,
+                                       cudaLaunchAttribute* attr)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(B * split));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = (size_t)a.L2s.smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)split;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+int coarse_sweep_clusters(const PathArgs& a, int split)
+{
+    if (!a.dim2 || split < 2) return 0;
+    if (cudaFuncSetAttribute(k_coarse_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.L2s.smem) !=
+        cudaSuccess)
+        return 0;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = split_config(a, 1, split, nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_coarse_sweep<true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, const double* Uold, double* Unew,
                                 const double* Fv, double* Gold, int init, const int* nfirst,
                                 const int* active, double* incr, cudaStream_t s)
 {
+    if (a.dim2 && a.split2d > 1) {
+        PathArgs as = slot(a, 1);
+        as.L2 = a.L2s;
+        cudaError_t e =
+            cudaFuncSetAttribute(k_coarse_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.L2s.smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = split_config(a, B, a.split2d, s, attr);
+        return cudaLaunchKernelEx(&cfg, k_coarse_sweep<true>, as, u0, Uold, Unew, Fv, Gold, init, nfirst, active,
+                                  incr);
+    }
     size_t sm = step_smem_bytes(a);
     return LAUNCH_STEP_KERNEL(k_coarse_sweep, B, sm, s, slot(a, 1), u0, Uold, Unew, Fv, Gold, init, nfirst,
                               active, incr);

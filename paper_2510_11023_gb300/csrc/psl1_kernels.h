@@ -32,7 +32,7 @@ struct SmemLayout {
 // 2D working arrays: each region lives in shared memory when it fits (in the
 // order listed: most used first), else in the CTA slot's global workspace.
 enum Region2D {
-    R2_BAD, R2_RED, R2_DINV, R2_PX, R2_PR, R2_PP, R2_PQ, R2_TAB32, R2_T1, R2_T2, R2_Z, R2_WD32,
+    R2_BAD, R2_RED, R2_SPLIT, R2_DINV, R2_PX, R2_PR, R2_PP, R2_PQ, R2_TAB32, R2_T1, R2_T2, R2_Z, R2_WD32,
     R2_N1, R2_N2, R2_CDF, R2_XR, R2_RHS, R2_CUR, R2_HIST, R2_NXT, R2_F, R2_WD, R2_COUNT
 };
 
@@ -43,8 +43,12 @@ struct Layout2D {
     long long gbytes;                // global workspace bytes per slot
 };
 
-// Kmax: modes; nT: max Mx (Qy + 1); nN: max Qx Qy; ntab: max Mx Qx/2 + My Qy/2.
-Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long ntab, int max_smem);
+// Kmax: modes; nT: max Mx (Qyl + 1); nN: max Qx Qyl (Qyl: the node columns of one
+// CTA, Qy unless the step is split); ntab: max Mx Qx/2 + My Qy/2; split > 1: the
+// step is shared by a cluster of that many CTAs (adds the partial-sum buffers,
+// always in shared memory).
+Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long ntab, int max_smem,
+                       int split = 1);
 
 // Pointers and sizes every solver kernel needs.
 struct PathArgs {
@@ -76,6 +80,9 @@ struct PathArgs {
     const double* bcc;       // coarse-substep weights mc^-a b(d + r/mc) (FP64), may be null
     const df* bccd;          // the same as double-float
     int* gmode;              // per instance: 1 if the stored G_old values are FP32-step values
+    double* corr;            // per-CTA-slot parareal corrections F_old(n) - G_old(n) of the sweep (Kmax)
+    int split2d;             // 2D: CTAs of the cluster that shares each coarse-sweep step (1: none)
+    Layout2D L2s;            // 2D: the layout of one CTA of such a cluster
 };
 
 // Kc: largest collocation K of the batch (0: none)
@@ -94,6 +101,9 @@ cudaError_t launch_fstage(const PathArgs& a, const double* Uold, double* Fv, con
 cudaError_t launch_coarse_sweep(const PathArgs& a, int B, const double* u0, const double* Uold, double* Unew,
                                 const double* Fv, double* Gold, int init, const int* nfirst,
                                 const int* active, double* incr, cudaStream_t s);
+// Clusters of `split` CTAs (with layout L2s) that can be resident at once for the 2D
+// coarse sweep (0 if none can, or the launch configuration is refused).
+int coarse_sweep_clusters(const PathArgs& a, int split);
 // G_old(n) = G_n(U_{0:n}) for every unit at given states (resumed parareal).
 cudaError_t launch_coarse_at(const PathArgs& a, const double* Uk, double* Gold, const int2* units, int nunits,
                              int* counter, int grid, cudaStream_t s);

@@ -22,6 +22,7 @@
 // residual of 1e-14.  Mixed path: CG in FP32 as the inner solver of an iterative
 // refinement whose residual rhs - (I + mu A) x is evaluated in double-float.
 #pragma once
+#include <cooperative_groups.h>
 #include "psl1_step.cuh"
 #include "psl1_step_mixed.cuh"
 #include "psl1_dfmath.cuh"
@@ -79,13 +80,16 @@ struct AxisOp {
 
 // Modes -> nodes along one axis for `rows` independent rows and up to two
 // components:  out(r, q) = E + O,  out(r, Q-1-q) = +-(E - O),  q < Qh, with
-// E, O the even- and odd-mode partial sums of in(r, c) tab(c, q).
+// E, O the even- and odd-mode partial sums of in(r, c) tab(c, q).  The table
+// rows are ts apart (ts = the axis' node-pair count; Qh may cover a sub-range
+// of its pairs, with tab pointing at the first of them and Q = 2 Qh the local
+// width of the output rows).
 //   in(r, c)  = in[r * irs + c * ics],  out(r, j) = out[r * ors + j * ojs]
 // and, if w is given, the result is multiplied by w(r, j) (strides of out).
 // RFAST: consecutive threads take consecutive rows (else consecutive pairs).
 template <class Nm, int RT, int QT, bool RFAST>
-__device__ void axis_fwd(int ncomp, AxisOp<Nm> o0, AxisOp<Nm> o1, int rows, int M, int Qh, int irs, int ics,
-                         int ors, int ojs, const typename Nm::V* w)
+__device__ void axis_fwd(int ncomp, AxisOp<Nm> o0, AxisOp<Nm> o1, int rows, int M, int Qh, int ts, int irs,
+                         int ics, int ors, int ojs, const typename Nm::V* w)
 {
     using V = typename Nm::V;
     using A = typename Nm::A;
@@ -119,7 +123,7 @@ __device__ void axis_fwd(int ncomp, AxisOp<Nm> o0, AxisOp<Nm> o1, int rows, int 
 #pragma unroll
             for (int c = 0; c < RT; ++c) a[c] = ip[c][(size_t)k * ics];
 #pragma unroll
-            for (int d = 0; d < QT; ++d) b[d] = tp[d][(size_t)k * Qh];
+            for (int d = 0; d < QT; ++d) b[d] = tp[d][(size_t)k * ts];
 #pragma unroll
             for (int c = 0; c < RT; ++c)
 #pragma unroll
@@ -127,7 +131,7 @@ __device__ void axis_fwd(int ncomp, AxisOp<Nm> o0, AxisOp<Nm> o1, int rows, int 
 #pragma unroll
             for (int c = 0; c < RT; ++c) a[c] = ip[c][(size_t)(k + 1) * ics];
 #pragma unroll
-            for (int d = 0; d < QT; ++d) b[d] = tp[d][(size_t)(k + 1) * Qh];
+            for (int d = 0; d < QT; ++d) b[d] = tp[d][(size_t)(k + 1) * ts];
 #pragma unroll
             for (int c = 0; c < RT; ++c)
 #pragma unroll
@@ -138,7 +142,7 @@ __device__ void axis_fwd(int ncomp, AxisOp<Nm> o0, AxisOp<Nm> o1, int rows, int 
 #pragma unroll
             for (int c = 0; c < RT; ++c) a[c] = ip[c][(size_t)k * ics];
 #pragma unroll
-            for (int d = 0; d < QT; ++d) b[d] = tp[d][(size_t)k * Qh];
+            for (int d = 0; d < QT; ++d) b[d] = tp[d][(size_t)k * ts];
 #pragma unroll
             for (int c = 0; c < RT; ++c)
 #pragma unroll
@@ -166,14 +170,15 @@ __device__ void axis_fwd(int ncomp, AxisOp<Nm> o0, AxisOp<Nm> o1, int rows, int 
 
 // Nodes -> modes along one axis:  out(r, c) = sum_{q < Qh} tab(c, q) (in(r, q) + s_c in(r, Q-1-q))
 // with s_c = (-1)^c for values, -(-1)^c for derivatives (c = 0-based mode),
-// +1 for squared tables (whose entries are squared on the fly).
+// +1 for squared tables (whose entries are squared on the fly).  Table rows
+// are ts apart; Qh may be a sub-range of the pairs (a partial sum), as in axis_fwd.
 //   in(r, j) = in[r * irs + j * ijs],  out(r, c) = out[r * ors + c * ocs].
 // sum = true: both components accumulate into o0.out; else each into its own.
 // Consecutive threads take consecutive rows; a thread owns CT consecutive
 // modes (CT even, so the parity of a mode is known at compile time).
 template <class Nm, int RT, int CT>
-__device__ void axis_bwd(int ncomp, bool sum, AxisOp<Nm> o0, AxisOp<Nm> o1, int rows, int M, int Qh, int irs,
-                         int ijs, int ors, int ocs)
+__device__ void axis_bwd(int ncomp, bool sum, AxisOp<Nm> o0, AxisOp<Nm> o1, int rows, int M, int Qh, int ts,
+                         int irs, int ijs, int ors, int ocs)
 {
     static_assert(CT % 2 == 0, "CT must be even");
     using V = typename Nm::V;
@@ -200,7 +205,7 @@ __device__ void axis_bwd(int ncomp, bool sum, AxisOp<Nm> o0, AxisOp<Nm> o1, int 
             for (int c = 0; c < RT; ++c) ip[c] = o.in + (size_t)(r[c] < rows ? r[c] : rows - 1) * irs;
             const V* tp[CT];
 #pragma unroll
-            for (int e = 0; e < CT; ++e) tp[e] = o.tab + (size_t)(c0 + e < M ? c0 + e : M - 1) * Qh;
+            for (int e = 0; e < CT; ++e) tp[e] = o.tab + (size_t)(c0 + e < M ? c0 + e : M - 1) * ts;
             // which fold each mode uses: s (sum) or d (difference)
             const bool sq = o.kind >= TV2;
             const bool even_sum = o.kind == TV;   // values: even c sums; derivatives: odd c sums
@@ -232,11 +237,28 @@ __device__ void axis_bwd(int ncomp, bool sum, AxisOp<Nm> o0, AxisOp<Nm> o1, int 
 }
 
 // ------------------------------------------------------------------ geometry and buffers
-struct Dims2 {
-    int Mx, My, Qx, Qy, Qhx, Qhy, Qyp, K;   // Qyp = Qy + 1: padded row of the Mx x Qy intermediates
+// A step split over the CTAs of a thread-block cluster (the 2D coarse sweep):
+// CTA `rank` of `size` owns the y node pairs [q0, q0 + nq) of the instance and
+// their mirrors, i.e. Qyl = 2 nq node columns.  Mode-space vectors are kept
+// whole in every CTA; every node-to-mode result (load, diagonal, operator
+// application) is a partial sum over the CTA's columns, added up across the
+// cluster through distributed shared memory (split_allreduce).  size = 1 is
+// the one-CTA step.
+struct Split {
+    int rank = 0, size = 1;
+    double* pb = nullptr;   // this CTA's partial-sum buffers in shared memory: 2 x stride 8-byte slots
+    int stride = 0;
+    int* nred = nullptr;    // shared: all-reductions done (selects the buffer)
 };
 
-__device__ __forceinline__ Dims2 dims2(const InstDev& I)
+struct Dims2 {
+    int Mx, My, Qx, Qy, Qhx, Qhy, K;
+    int q0, nq;   // this CTA's y node pairs
+    int Qyl;      // its node columns (2 nq; Qy for a one-CTA step)
+    int Qyp;      // Qyl + 1: padded row of the Mx x Qyl intermediates
+};
+
+__device__ __forceinline__ Dims2 dims2(const InstDev& I, const Split& sp = Split{})
 {
     Dims2 g;
     g.Mx = I.Mx;
@@ -245,9 +267,43 @@ __device__ __forceinline__ Dims2 dims2(const InstDev& I)
     g.Qy = I.Qy;
     g.Qhx = I.Qh;
     g.Qhy = I.Qhy;
-    g.Qyp = I.Qy + 1;
     g.K = I.K;
+    const int nqb = (I.Qhy + sp.size - 1) / sp.size;
+    g.q0 = min(I.Qhy, sp.rank * nqb);
+    g.nq = min(nqb, I.Qhy - g.q0);
+    g.Qyl = 2 * g.nq;
+    g.Qyp = g.Qyl + 1;
     return g;
+}
+
+// global y node of local column jl (columns jl < nq are pairs q0 + jl, the rest their mirrors)
+__device__ __forceinline__ int col_global(const Dims2& g, int jl)
+{
+    return jl < g.nq ? g.q0 + jl : g.Qy - g.Qyl - g.q0 + jl;
+}
+
+// Sum of the CTAs' partial vectors v (K, this CTA's partial on entry, the
+// cluster's sum on return, the same in every CTA: each adds the partials in
+// rank order).  The buffers alternate between calls; a call writes the buffer
+// the call before the last one read, and the cluster barrier of the call in
+// between orders the two.
+template <class Nm>
+__device__ void split_allreduce(const Split& sp, typename Nm::V* v, int K)
+{
+    if (sp.size <= 1) return;
+    using V = typename Nm::V;
+    namespace cgx = cooperative_groups;
+    cgx::cluster_group cl = cgx::this_cluster();
+    V* mine = reinterpret_cast<V*>(sp.pb + (size_t)(*sp.nred & 1) * sp.stride);
+    for (int k = threadIdx.x; k < K; k += NT) mine[k] = v[k];
+    cl.sync();
+    for (int k = threadIdx.x; k < K; k += NT) {
+        V acc = *cl.map_shared_rank(mine + k, 0);
+        for (int r = 1; r < sp.size; ++r) acc = Nm::add(acc, *cl.map_shared_rank(mine + k, r));
+        v[k] = acc;
+    }
+    if (threadIdx.x == 0) ++*sp.nred;   // every thread read the count above, before cl.sync()
+    __syncthreads();
 }
 
 template <class Nm>
@@ -270,61 +326,71 @@ struct Step2D {
     void* red;                    // reduction scratch (2 NT/32 doubles)
 };
 
-// A v -> out (K): the four folded one-axis transforms
+// A v -> out (K): the four folded one-axis transforms.
+// Node arrays hold the CTA's columns: N(i, jl) at i * Qyl + jl; the Mx x Qyl
+// intermediates have rows Qyp apart.  Transforms along y use the y tables from
+// the CTA's first pair on (row stride Qhy).
 template <class Nm, int RT, int QT, int CT>
 __device__ void op_apply(const Dims2& g, const Tabs2<Nm>& tb, const typename Nm::V* v, const typename Nm::V* W,
                          typename Nm::V* T1, typename Nm::V* T2, typename Nm::V* N1, typename Nm::V* N2,
-                         typename Nm::V* out)
+                         typename Nm::V* out, const Split& sp = Split{})
 {
+    const typename Nm::V *Sy = tb.Sy + g.q0, *Dy = tb.Dy + g.q0;
     // along y: T1 = v . Sy (values), T2 = v . Dy (derivatives);  rows k < Mx
-    axis_fwd<Nm, RT, QT, false>(2, {v, tb.Sy, T1, TV}, {v, tb.Dy, T2, TD}, g.Mx, g.My, g.Qhy, g.My, 1, g.Qyp, 1,
+    axis_fwd<Nm, RT, QT, false>(2, {v, Sy, T1, TV}, {v, Dy, T2, TD}, g.Mx, g.My, g.nq, g.Qhy, g.My, 1, g.Qyp, 1,
                                 nullptr);
     __syncthreads();
-    // along x, times W: N1 = W o (Dx . T1) = W o dx v,  N2 = W o (Sx . T2) = W o dy v;  rows j < Qy
-    axis_fwd<Nm, RT, QT, true>(2, {T1, tb.Dx, N1, TD}, {T2, tb.Sx, N2, TV}, g.Qy, g.Mx, g.Qhx, 1, g.Qyp, 1, g.Qy,
-                               W);
+    // along x, times W: N1 = W o (Dx . T1) = W o dx v,  N2 = W o (Sx . T2) = W o dy v;  rows: the CTA's columns
+    axis_fwd<Nm, RT, QT, true>(2, {T1, tb.Dx, N1, TD}, {T2, tb.Sx, N2, TV}, g.Qyl, g.Mx, g.Qhx, g.Qhx, 1, g.Qyp,
+                               1, g.Qyl, W);
     __syncthreads();
     // back along x: T1 = Dx^T N1, T2 = Sx^T N2
-    axis_bwd<Nm, RT, CT>(2, false, {N1, tb.Dx, T1, TD}, {N2, tb.Sx, T2, TV}, g.Qy, g.Mx, g.Qhx, 1, g.Qy, 1, g.Qyp);
+    axis_bwd<Nm, RT, CT>(2, false, {N1, tb.Dx, T1, TD}, {N2, tb.Sx, T2, TV}, g.Qyl, g.Mx, g.Qhx, g.Qhx, 1, g.Qyl,
+                         1, g.Qyp);
     __syncthreads();
-    // back along y, summed: out = T1 . Sy^T + T2 . Dy^T
-    axis_bwd<Nm, 1, CT>(2, true, {T1, tb.Sy, out, TV}, {T2, tb.Dy, nullptr, TD}, g.Mx, g.My, g.Qhy, g.Qyp, 1, g.My,
+    // back along y, summed: out = T1 . Sy^T + T2 . Dy^T (over the CTA's columns)
+    axis_bwd<Nm, 1, CT>(2, true, {T1, Sy, out, TV}, {T2, Dy, nullptr, TD}, g.Mx, g.My, g.nq, g.Qhy, g.Qyp, 1, g.My,
                         1);
     __syncthreads();
+    split_allreduce<Nm>(sp, out, g.K);
 }
 
-// values at the nodes: N = Sx . (v . Sy)
+// values at the CTA's nodes: N = Sx . (v . Sy)
 template <class Nm, int RT, int QT>
 __device__ void to_nodes(const Dims2& g, const Tabs2<Nm>& tb, const typename Nm::V* v, typename Nm::V* T1,
                          typename Nm::V* N)
 {
-    axis_fwd<Nm, RT, QT, false>(1, {v, tb.Sy, T1, TV}, {}, g.Mx, g.My, g.Qhy, g.My, 1, g.Qyp, 1, nullptr);
+    axis_fwd<Nm, RT, QT, false>(1, {v, tb.Sy + g.q0, T1, TV}, {}, g.Mx, g.My, g.nq, g.Qhy, g.My, 1, g.Qyp, 1,
+                                nullptr);
     __syncthreads();
-    axis_fwd<Nm, RT, QT, true>(1, {T1, tb.Sx, N, TV}, {}, g.Qy, g.Mx, g.Qhx, 1, g.Qyp, 1, g.Qy, nullptr);
+    axis_fwd<Nm, RT, QT, true>(1, {T1, tb.Sx, N, TV}, {}, g.Qyl, g.Mx, g.Qhx, g.Qhx, 1, g.Qyp, 1, g.Qyl, nullptr);
     __syncthreads();
 }
 
 // Galerkin projection of node values: out_kl = sum_ij phi_k(x_i) phi_l(y_j) N_ij
 template <class Nm, int RT, int CT>
 __device__ void from_nodes(const Dims2& g, const Tabs2<Nm>& tb, const typename Nm::V* N, typename Nm::V* T1,
-                           typename Nm::V* out)
+                           typename Nm::V* out, const Split& sp = Split{})
 {
-    axis_bwd<Nm, RT, CT>(1, false, {N, tb.Sx, T1, TV}, {}, g.Qy, g.Mx, g.Qhx, 1, g.Qy, 1, g.Qyp);
+    axis_bwd<Nm, RT, CT>(1, false, {N, tb.Sx, T1, TV}, {}, g.Qyl, g.Mx, g.Qhx, g.Qhx, 1, g.Qyl, 1, g.Qyp);
     __syncthreads();
-    axis_bwd<Nm, 1, CT>(1, false, {T1, tb.Sy, out, TV}, {}, g.Mx, g.My, g.Qhy, g.Qyp, 1, g.My, 1);
+    axis_bwd<Nm, 1, CT>(1, false, {T1, tb.Sy + g.q0, out, TV}, {}, g.Mx, g.My, g.nq, g.Qhy, g.Qyp, 1, g.My, 1);
     __syncthreads();
+    split_allreduce<Nm>(sp, out, g.K);
 }
 
 // diag(A)_kl = sum_ij W_ij (phi_k'(x_i)^2 phi_l(y_j)^2 + phi_k(x_i)^2 phi_l'(y_j)^2) -> out
 template <class Nm, int RT, int CT>
 __device__ void op_diag(const Dims2& g, const Tabs2<Nm>& tb, const typename Nm::V* W, typename Nm::V* T1,
-                        typename Nm::V* T2, typename Nm::V* out)
+                        typename Nm::V* T2, typename Nm::V* out, const Split& sp = Split{})
 {
-    axis_bwd<Nm, RT, CT>(2, false, {W, tb.Dx, T1, TD2}, {W, tb.Sx, T2, TV2}, g.Qy, g.Mx, g.Qhx, 1, g.Qy, 1, g.Qyp);
+    axis_bwd<Nm, RT, CT>(2, false, {W, tb.Dx, T1, TD2}, {W, tb.Sx, T2, TV2}, g.Qyl, g.Mx, g.Qhx, g.Qhx, 1, g.Qyl,
+                         1, g.Qyp);
     __syncthreads();
-    axis_bwd<Nm, 1, CT>(2, true, {T1, tb.Sy, out, TV2}, {T2, tb.Dy, nullptr, TD2}, g.Mx, g.My, g.Qhy, g.Qyp, 1, g.My,
-                        1);
+    axis_bwd<Nm, 1, CT>(2, true, {T1, tb.Sy + g.q0, out, TV2}, {T2, tb.Dy + g.q0, nullptr, TD2}, g.Mx, g.My, g.nq,
+                        g.Qhy, g.Qyp, 1, g.My, 1);
     __syncthreads();
+    split_allreduce<Nm>(sp, out, g.K);
 }
 
 // ------------------------------------------------------------------ families at a 2D node
@@ -436,9 +502,13 @@ __device__ __forceinline__ T block_maxT(T v, T* red)
 // residuals can be ~1e-15 of the solution, whose FP32 inner products would
 // underflow unscaled.  flag[0]: set to 0 when p . (I + mu A) p <= 0 (not SPD);
 // flag[1] counts operator applications.
+// With a split step every CTA of the cluster runs the whole iteration on the
+// whole vectors (identical values, so identical control flow); only the
+// operator application is shared (op_apply's all-reduction).
 template <class Nm, int RT, int QT, int CT>
 __device__ void pcg2d(const Dims2& g, const Tabs2<Nm>& tb, typename Nm::V mu, const typename Nm::V* W,
-                      typename Nm::V* b, const Step2D& S, int* flag, int maxit, typename Nm::V rtol)
+                      typename Nm::V* b, const Step2D& S, int* flag, int maxit, typename Nm::V rtol,
+                      const Split& sp = Split{})
 {
     using T = typename Nm::V;
     const int K = g.K, tid = threadIdx.x;
@@ -474,7 +544,7 @@ __device__ void pcg2d(const Dims2& g, const Tabs2<Nm>& tb, typename Nm::V mu, co
     const T stop = rtol * rtol * rr;
     for (int it = 0; it < maxit && rr > T(0); ++it) {
         if (tid == 0) flag[1] += 1;
-        op_apply<Nm, RT, QT, CT>(g, tb, p, W, T1, T2, N1, N2, q);
+        op_apply<Nm, RT, QT, CT>(g, tb, p, W, T1, T2, N1, N2, q, sp);
         T pq = 0, zero = 0;
         for (int k = tid; k < K; k += NT) {
             T qk = p[k] + mu * q[k];
@@ -537,10 +607,10 @@ __device__ __forceinline__ Tabs2<NumF> stage_tab32(const InstDev& I, const TabDe
 // FP64 path.  c, hist: K (any memory); out, F: K.  Returns the first bad index or -1.
 __device__ int step2d_fp64(const InstDev& I, const TabDev& TX, const TabDev& TY, const double* tp,
                            const double* c, const double* hist, double te, double mu, double* out, double* F,
-                           const Step2D& S, int* flag)
+                           const Step2D& S, int* flag, const Split& sp = Split{})
 {
-    const Dims2 g = dims2(I);
-    const int tid = threadIdx.x, QQ = g.Qx * g.Qy;
+    const Dims2 g = dims2(I, sp);
+    const int tid = threadIdx.x, QQ = g.Qx * g.Qyl;
     const Tabs2<NumD> tb{tp + TX.oSt, tp + TX.oDt, tp + TY.oSt, tp + TY.oDt};
     double* T1 = static_cast<double*>(S.T1);
     double* T2 = static_cast<double*>(S.T2);
@@ -551,31 +621,31 @@ __device__ int step2d_fp64(const InstDev& I, const TabDev& TX, const TabDev& TY,
     if (tid == 0) flag[0] = -1;
     to_nodes<NumD, 2, 2>(g, tb, c, T1, N1);
     for (int e = tid; e < QQ; e += NT) {
-        const int i = e / g.Qy, j = e - i * g.Qy;
+        const int i = e / g.Qyl, j = col_global(g, e - i * g.Qyl);
         const Node2 nd = node2(I, TX, TY, tp, i, j);
         const double u = N1[e];
         W[e] = nd.w * D_eval2(I, nd.sx1, nd.sx2, nd.cy2, u);
         N2[e] = nd.w * f_eval(I, nd.x, nd.sx1, te, u);
     }
     __syncthreads();
-    from_nodes<NumD, 2, 2>(g, tb, N2, T2, F);
-    op_diag<NumD, 2, 2>(g, tb, W, T1, T2, dinv);
+    from_nodes<NumD, 2, 2>(g, tb, N2, T2, F, sp);
+    op_diag<NumD, 2, 2>(g, tb, W, T1, T2, dinv, sp);
     for (int k = tid; k < g.K; k += NT) {
         dinv[k] = 1.0 / (1.0 + mu * dinv[k]);
         out[k] = hist[k] + mu * F[k];
     }
     __syncthreads();
-    pcg2d<NumD, 2, 2, 2>(g, tb, mu, W, out, S, flag, PCG2_MAXIT64, PCG2_RTOL64);
+    pcg2d<NumD, 2, 2, 2>(g, tb, mu, W, out, S, flag, PCG2_MAXIT64, PCG2_RTOL64, sp);
     return flag[0];
 }
 
 // Mixed path (fp32_only: FP32 coefficients and a single FP32 solve).
 __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY, const double* tp,
                             const double* c, const double* hist, double te, double mu, double* out, double* F,
-                            const Step2D& S, int* flag, bool fp32_only)
+                            const Step2D& S, int* flag, bool fp32_only, const Split& sp = Split{})
 {
-    const Dims2 g = dims2(I);
-    const int tid = threadIdx.x, QQ = g.Qx * g.Qy, K = g.K;
+    const Dims2 g = dims2(I, sp);
+    const int tid = threadIdx.x, QQ = g.Qx * g.Qyl, K = g.K;
     const Tabs2<NumDF> td{reinterpret_cast<const df*>(tp + TX.oStd), reinterpret_cast<const df*>(tp + TX.oDtd),
                           reinterpret_cast<const df*>(tp + TY.oStd), reinterpret_cast<const df*>(tp + TY.oDtd)};
     df* T1 = static_cast<df*>(S.T1);
@@ -591,7 +661,7 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
     to_nodes<NumDF, 2, 2>(g, td, S.cdf, T1, N1);
     const df emt = (I.fpar[3] != 0.0 && !fp32_only) ? df_from_double(exp(-te)) : df{0.f, 0.f};
     for (int e = tid; e < QQ; e += NT) {
-        const int i = e / g.Qy, j = e - i * g.Qy;
+        const int i = e / g.Qyl, j = col_global(g, e - i * g.Qyl);
         if (fp32_only) {
             const Node2 nd = node2(I, TX, TY, tp, i, j);
             const double u = df_to_double(N1[e]);
@@ -618,10 +688,10 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
         N2[e] = wf;
     }
     __syncthreads();
-    from_nodes<NumDF, 2, 2>(g, td, N2, T2, S.cdf);
+    from_nodes<NumDF, 2, 2>(g, td, N2, T2, S.cdf, sp);
     // FP32 Jacobi diagonal (into the CG's dinv)
     float* dinv = static_cast<float*>(S.dinv);
-    op_diag<NumF, 2, 4>(g, tf, S.wd32, static_cast<float*>(S.T1), static_cast<float*>(S.T2), dinv);
+    op_diag<NumF, 2, 4>(g, tf, S.wd32, static_cast<float*>(S.T1), static_cast<float*>(S.T2), dinv, sp);
     for (int k = tid; k < K; k += NT) {
         F[k] = df_to_double(S.cdf[k]);
         dinv[k] = 1.0f / (1.0f + (float)mu * dinv[k]);
@@ -632,7 +702,7 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
     }
     __syncthreads();
     const float rtol = fp32_only ? PCG2_RTOL32 : I.inner_rtol;   // tunable in the refined step
-    pcg2d<NumF, 2, 4, 4>(g, tf, (float)mu, S.wd32, S.z, S, flag, PCG2_MAXIT32, rtol);
+    pcg2d<NumF, 2, 4, 4>(g, tf, (float)mu, S.wd32, S.z, S, flag, PCG2_MAXIT32, rtol, sp);
     float zprev = 0.f;
     for (int sweep = 0;; ++sweep) {
         float zmax = 0.f, xmax = 0.f;
@@ -653,11 +723,11 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
         // residual rhs - (I + mu A) x with A applied in double-float
         for (int k = tid; k < K; k += NT) S.cdf[k] = df_from_double(S.xr[k]);
         __syncthreads();
-        op_apply<NumDF, 2, 2, 2>(g, td, S.cdf, W, T1, T2, N1, N2, S.cdf);
+        op_apply<NumDF, 2, 2, 2>(g, td, S.cdf, W, T1, T2, N1, N2, S.cdf, sp);
         for (int k = tid; k < K; k += NT)
             S.z[k] = (float)(S.rhs[k] - S.xr[k] - mu * df_to_double(S.cdf[k]));
         __syncthreads();
-        pcg2d<NumF, 2, 4, 4>(g, tf, (float)mu, S.wd32, S.z, S, flag, PCG2_MAXIT32, rtol);
+        pcg2d<NumF, 2, 4, 4>(g, tf, (float)mu, S.wd32, S.z, S, flag, PCG2_MAXIT32, rtol, sp);
     }
     for (int k = tid; k < K; k += NT) out[k] = S.xr[k];
     __syncthreads();

@@ -73,6 +73,8 @@ SIGNATURES = {
     "psl1_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "psl1_set_inexact_fine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "psl1_set_coarse_substeps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "psl1_set_sweep_split": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "psl1_get_sweep_split": (ctypes.c_int, [ctypes.c_void_p, _I]),
     "psl1_get_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D]),
     "psl1_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "psl1_get_soe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, _D, ctypes.c_int,
@@ -332,6 +334,15 @@ class Problem:
         _chk(self.L.psl1_assemble(self.h, b, {"tensor": 0, "moments": 1}[method], units, _dp(D),
                                   A.ctypes.data_as(_F), ctypes.byref(ms)), self.h)
         return A, ms.value
+
+    def set_sweep_split(self, ctas: int = 0):
+        """2D: share each coarse-sweep step among a cluster of `ctas` CTAs (1, 2, 4, 8; 0: automatic)."""
+        _chk(self.L.psl1_set_sweep_split(self.h, int(ctas)), self.h)
+
+    def sweep_split(self) -> int:
+        n = ctypes.c_int(0)
+        _chk(self.L.psl1_get_sweep_split(self.h, ctypes.byref(n)), self.h)
+        return n.value
 
     def set_coarse_substeps(self, c: int):
         """L1 substeps per slice of the coarse propagator (1: the paper's one-step G)."""
