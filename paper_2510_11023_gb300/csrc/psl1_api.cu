@@ -56,7 +56,7 @@ struct psl1_problem {
     std::vector<void*> allocs;
     InstDev* d_inst = nullptr;
     TabDev* d_tab = nullptr;
-    double *d_tp = nullptr, *d_bp = nullptr, *d_bpd = nullptr, *d_dud = nullptr, *d_u0 = nullptr;
+    double *d_tp = nullptr, *d_bp = nullptr, *d_bpd = nullptr, *d_dud = nullptr, *d_u0 = nullptr, *d_hc = nullptr;
     double *d_Ua = nullptr, *d_Ub = nullptr, *d_Us = nullptr, *d_Fv = nullptr, *d_Gold = nullptr;
     double *d_incr = nullptr, *d_work = nullptr, *d_ring = nullptr, *d_corr = nullptr;
     int *d_nfirst = nullptr, *d_active = nullptr, *d_counter = nullptr;
@@ -568,6 +568,9 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     // mixed-path coarse differences (double-float, 8 bytes per entry)
     long long dud_stride = precision == PSL1_PREC_FP64 ? 0 : (long long)P * h->Kmax;
     if (dud_stride) CTRY(dalloc(h, &h->d_dud, (size_t)nslots * dud_stride));
+    // coarse-history terms of a slice's steps (double-float, 8 bytes per entry)
+    long long hc_stride = precision == PSL1_PREC_FP64 ? 0 : (long long)h->mmax * h->Kmax;
+    if (hc_stride) CTRY(dalloc(h, &h->d_hc, (size_t)nslots * hc_stride));
     // fine units, longest first (cost ~ m K^3)
     std::vector<int2> units;
     for (int b = 0; b < batch; ++b)
@@ -638,6 +641,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.bpd = reinterpret_cast<const df*>(h->d_bpd);
     a.dud = reinterpret_cast<df*>(h->d_dud);
     a.dud_stride = dud_stride;
+    a.hc = reinterpret_cast<df*>(h->d_hc);
+    a.hc_stride = hc_stride;
     a.status = h->d_status;
     a.work = h->d_work;
     a.work_stride = work_stride;

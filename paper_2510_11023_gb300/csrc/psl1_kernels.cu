@@ -338,9 +338,15 @@ __device__ __forceinline__ SliceGrid substep_grid(const PathArgs& a, const InstD
 // F_n of instance ii on coarse states U (rows 0..n, global): g.m steps with
 // the local fine history kept in the CTA's ring and the coarse history
 // m^-a sum_{i=1}^n b(n-i+r/m) (U_i - U_{i-1})  (Eq. L1Fine, difference form).
+// Fine steps of one slice served by one pass over the coarse differences when
+// the coarse-history terms are formed ahead of the steps.
+constexpr int HC_R = 8;
+
+// dud_ready: the caller has already stored the coarse differences of rows
+// 0..n-1 in the CTA's slot (a sweep appends one row per step).
 template <bool D2>
 __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, double* Vout, double* out,
-                           Carve& cv, double* ring, bool one_solve, const SliceGrid& g)
+                           Carve& cv, double* ring, bool one_solve, const SliceGrid& g, bool dud_ready = false)
 {
     const InstDev& I = a.inst[ii];
     const int K = I.K, m = g.m, tid = threadIdx.x;
@@ -358,9 +364,34 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
         cv.cur[k] = U[(size_t)n * K + k];
         if (Vout) Vout[k] = cv.cur[k];
     }
-    if (dfh)
+    if (dfh && !dud_ready)
         for (int e = tid; e < n * K; e += NT) dud[e] = df_from_double(U[e + K] - U[e]);
     __syncthreads();
+    // The coarse-history terms of all m steps, m^-a sum_i b(n-i+r/m) (U_i - U_{i-1}),
+    // formed ahead of the steps, HC_R steps per pass over the differences: the
+    // differences are read m / HC_R times per slice instead of once per step.  Each
+    // thread later reads the entries it wrote (the same k), so no barrier is needed.
+    df* hc = (dfh && a.hc) ? a.hc + (size_t)blockIdx.x * a.hc_stride : nullptr;
+    if (hc && n > 0) {
+        for (int r0 = 0; r0 < m; r0 += HC_R) {
+            const int nr = m - r0 < HC_R ? m - r0 : HC_R;
+            for (int k = tid; k < K; k += NT) {
+                dfacc acc[HC_R];
+#pragma unroll
+                for (int q = 0; q < HC_R; ++q) acc[q] = dfacc{0.f, 0.f};
+                for (int i = 1; i <= n; ++i) {
+                    const df d = dud[(size_t)(i - 1) * K + k];
+                    const df* bc = bCd + (size_t)(n - i) * m + r0;
+#pragma unroll
+                    for (int q = 0; q < HC_R; ++q)
+                        if (q < nr) dfacc_fma(acc[q], bc[q], d);
+                }
+#pragma unroll
+                for (int q = 0; q < HC_R; ++q)
+                    if (q < nr) hc[(size_t)(r0 + q) * K + k] = dfacc_result(acc[q]);
+            }
+        }
+    }
     for (int r = 1; r <= m; ++r) {
         for (int k = tid; k < K && dfh; k += NT) {
             // four independent partial sums (the loads of a term do not wait on the previous one)
@@ -373,15 +404,19 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
                 dfacc_fma(a3, bFd[r - j - 3], ringd[(size_t)(j + 2) * K + k]);
             }
             for (; j <= r - 1; ++j) dfacc_fma(a0, bFd[r - j], ringd[(size_t)(j - 1) * K + k]);
-            const df* bc = bCd + (r - 1);
-            int i = 1;
-            for (; i + 3 <= n; i += 4) {
-                dfacc_fma(a0, bc[(size_t)(n - i) * m], dud[(size_t)(i - 1) * K + k]);
-                dfacc_fma(a1, bc[(size_t)(n - i - 1) * m], dud[(size_t)i * K + k]);
-                dfacc_fma(a2, bc[(size_t)(n - i - 2) * m], dud[(size_t)(i + 1) * K + k]);
-                dfacc_fma(a3, bc[(size_t)(n - i - 3) * m], dud[(size_t)(i + 2) * K + k]);
+            if (hc) {
+                if (n > 0) dfacc_add(a0, hc[(size_t)(r - 1) * K + k]);
+            } else {
+                const df* bc = bCd + (r - 1);
+                int i = 1;
+                for (; i + 3 <= n; i += 4) {
+                    dfacc_fma(a0, bc[(size_t)(n - i) * m], dud[(size_t)(i - 1) * K + k]);
+                    dfacc_fma(a1, bc[(size_t)(n - i - 1) * m], dud[(size_t)i * K + k]);
+                    dfacc_fma(a2, bc[(size_t)(n - i - 2) * m], dud[(size_t)(i + 1) * K + k]);
+                    dfacc_fma(a3, bc[(size_t)(n - i - 3) * m], dud[(size_t)(i + 2) * K + k]);
+                }
+                for (; i <= n; ++i) dfacc_fma(a0, bc[(size_t)(n - i) * m], dud[(size_t)(i - 1) * K + k]);
             }
-            for (; i <= n; ++i) dfacc_fma(a0, bc[(size_t)(n - i) * m], dud[(size_t)(i - 1) * K + k]);
             dfacc_add(a0, dfacc_result(a1));
             dfacc_add(a2, dfacc_result(a3));
             dfacc_add(a0, dfacc_result(a2));
@@ -469,8 +504,11 @@ __device__ void learned_correction(const PathArgs& a, const InstDev& I, int n, C
 // G_n of instance ii on U (rows 0..n, global) -> cv.nxt.  History in the
 // difference form U_n - sum_{j=0}^{n-1} b_{n-j} (U_{j+1} - U_j) of Eq. L1Scheme.
 // one_solve: the FP32 step (inexact early iterations; MIXED handles).
+// dud_ready: the coarse differences of rows 0..n-1 are already in the CTA's
+// slot (FP32-pipe paths; the sweep appends one row per step).
 template <bool D2>
-__device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, Carve& cv, bool one_solve = false)
+__device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, Carve& cv, bool one_solve = false,
+                            bool dud_ready = false)
 {
     const InstDev& I = a.inst[ii];
     const int K = I.K, tid = threadIdx.x;
@@ -478,15 +516,39 @@ __device__ void coarse_step(const PathArgs& a, int ii, int n, const double* U, C
         // G with mc L1 substeps per slice: the fine propagator on the substep grid
         // (the CTA's ring slot holds its local history); result in cv.nxt
         double* ring = a.ring + (size_t)blockIdx.x * a.ring_stride;
-        fine_slice<D2>(a, ii, n, U, nullptr, cv.nxt, cv, ring, one_solve, substep_grid(a, I));
+        fine_slice<D2>(a, ii, n, U, nullptr, cv.nxt, cv, ring, one_solve, substep_grid(a, I), dud_ready);
         return;
     }
-    const double* bF = a.bp + I.oB;
-    for (int k = tid; k < K; k += NT) {
-        double c = U[(size_t)n * K + k], h = c;
-        for (int j = 0; j < n; ++j) h -= bF[n - j] * (U[(size_t)(j + 1) * K + k] - U[(size_t)j * K + k]);
-        cv.cur[k] = c;
-        cv.hist[k] = h;
+    if (a.prec != 0) {
+        // FP32-pipe paths: the history sum in double-float over the stored differences
+        // (on GB300 an FP64 operation costs 64 FP32 lanes; this sum is n K terms per step)
+        df* dud = a.dud + (size_t)blockIdx.x * a.dud_stride;
+        const df* bFd = a.bpd + I.oB;
+        if (!dud_ready) {
+            for (int e = tid; e < n * K; e += NT) dud[e] = df_from_double(U[e + K] - U[e]);
+            __syncthreads();
+        }
+        for (int k = tid; k < K; k += NT) {
+            dfacc a0{0.f, 0.f}, a1{0.f, 0.f};
+            int j = 0;
+            for (; j + 1 < n; j += 2) {
+                dfacc_fma(a0, bFd[n - j], dud[(size_t)j * K + k]);
+                dfacc_fma(a1, bFd[n - j - 1], dud[(size_t)(j + 1) * K + k]);
+            }
+            if (j < n) dfacc_fma(a0, bFd[n - j], dud[(size_t)j * K + k]);
+            dfacc_add(a0, dfacc_result(a1));
+            const double c = U[(size_t)n * K + k];
+            cv.cur[k] = c;
+            cv.hist[k] = c - df_to_double(dfacc_result(a0));
+        }
+    } else {
+        const double* bF = a.bp + I.oB;
+        for (int k = tid; k < K; k += NT) {
+            double c = U[(size_t)n * K + k], h = c;
+            for (int j = 0; j < n; ++j) h -= bF[n - j] * (U[(size_t)(j + 1) * K + k] - U[(size_t)j * K + k]);
+            cv.cur[k] = c;
+            cv.hist[k] = h;
+        }
     }
     if (tid == 0 && a.flops && cv.sp.rank == 0) atomicAdd(a.flops + a.flop_slot, 2.0 * K * n);
     __syncthreads();
@@ -703,10 +765,22 @@ k_coarse_sweep(PathArgs a, const double* u0, const double* Uold, double* Unew, c
     // cluster barriers inside the step order all reads of the old value before any
     // write of the new one (each thread keeps its own k, so no block barrier is needed)
     double* corr = a.corr + (size_t)blockIdx.x * a.Kmax;
+    // FP32-pipe paths: the coarse differences U_{i+1} - U_i as double-float rows in the
+    // CTA's slot, rows < n0 now and one more row per step (not n rows per step)
+    df* dud = a.prec != 0 ? a.dud + (size_t)blockIdx.x * a.dud_stride : nullptr;
+    if (dud) {
+        for (int e = tid; e < n0 * K; e += NT) dud[e] = df_from_double(U[e + K] - U[e]);
+        __syncthreads();
+    }
     for (int n = n0; n < P; ++n) {
+        if (dud && n > n0) {
+            for (int k = tid; k < K; k += NT)
+                dud[(size_t)(n - 1) * K + k] = df_from_double(U[(size_t)n * K + k] - U[(size_t)(n - 1) * K + k]);
+            __syncthreads();
+        }
         if (!init)
             for (int k = tid; k < K; k += NT) corr[k] = Fo[(size_t)n * K + k] - Go[(size_t)n * K + k];
-        coarse_step<D2>(a, ii, n, U, cv, g32);
+        coarse_step<D2>(a, ii, n, U, cv, g32, dud != nullptr);
         for (int k = tid; k < K; k += NT) {
             double g = cv.nxt[k];
             size_t e = (size_t)n * K + k;
@@ -771,8 +845,18 @@ k_serial_hyb(PathArgs a, const double* u0, double* Us)
     double* ring = a.ring + (size_t)blockIdx.x * a.ring_stride;
     for (int k = threadIdx.x; k < I.K; k += NT) U[k] = u0[I.oK + k];
     __syncthreads();
-    for (int n = 0; n < I.P; ++n)
-        fine_slice<D2>(a, ii, n, U, nullptr, U + (size_t)(n + 1) * I.K, cv, ring, false, fine_grid(a, I));
+    // FP32-pipe paths: one more row of coarse differences per slice (not n rows)
+    df* dud = a.prec != 0 ? a.dud + (size_t)blockIdx.x * a.dud_stride : nullptr;
+    for (int n = 0; n < I.P; ++n) {
+        if (dud && n > 0) {
+            for (int k = threadIdx.x; k < I.K; k += NT)
+                dud[(size_t)(n - 1) * I.K + k] =
+                    df_from_double(U[(size_t)n * I.K + k] - U[(size_t)(n - 1) * I.K + k]);
+            __syncthreads();
+        }
+        fine_slice<D2>(a, ii, n, U, nullptr, U + (size_t)(n + 1) * I.K, cv, ring, false, fine_grid(a, I),
+                       dud != nullptr);
+    }
 }
 
 __global__ void k_uni_init(const InstDev* inst, const double* u0, double* Wcur, double* Us)
@@ -1102,6 +1186,7 @@ cudaError_t launch_one_slice_noalloc(const PathArgs& a, double* scratch, int b, 
     a2.work_stride = work_r;
     a2.dud = reinterpret_cast<df*>(scratch + ring_r + work_r);
     a2.dud_stride = dud_doubles;
+    a2.hc = nullptr;   // the per-step coarse-history sums: no scratch beyond the fixed array
     a2.nslots = 1;
     size_t sm = step_smem_bytes(a2);
     return a.dim2 ? launch_k(k_one_slice_noalloc<true>, 1, sm, s, a2, b, n, U, V)

@@ -59,6 +59,8 @@ struct PathArgs {
     const df* bpd;           // the same weights as double-float (mixed history sums)
     df* dud;                 // per-CTA-slot coarse differences U_i - U_{i-1} (P x Kmax, double-float)
     long long dud_stride;
+    df* hc;                  // per-CTA-slot coarse-history terms of a slice's m steps (mmax x Kmax), may be null
+    long long hc_stride;
     DevStatus* status;
     double* work;            // per-CTA-slot workspace (FP64 factor; 2D arrays outside shared memory)
     long long work_stride;   // doubles per slot
