@@ -37,7 +37,7 @@ METRIC = "parareal wall-time to rel err 1e-8 vs serial GPU solve; fine steps*mod
 UNIT = "fine_steps*modes/s"
 TARGET = 1e-8
 FIXED_TOL = TARGET             # increment tolerance of the stopping rule, fixed in advance
-INEXACT_ABOVE = (1e-4, 1e-5)   # increments above which early F stages take the FP32 step (candidates)
+INEXACT_ABOVE = (1e-4, 1e-5, 3e-6)   # increments above which early iterations take the FP32 step (candidates)
 
 
 def parse():
@@ -72,7 +72,7 @@ def parse():
                          "learned correction; auto: the fastest to rel err 1e-8 in warm-up")
     ap.add_argument("--inexact", default="auto", choices=["auto", "on", "off"],
                     help="inexact early iterations (the FP32 step on slices not yet exact while the increment "
-                         "exceeds a threshold, 1e-4 or 1e-5; mixed); auto: the fastest to rel err 1e-8 in warm-up")
+                         "exceeds a threshold, 1e-4, 1e-5 or 3e-6; mixed); auto: the fastest to rel err 1e-8 in warm-up")
     ap.add_argument("--sweep-split", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="2D: CTAs of the cluster that shares each coarse-sweep step (0: the library's choice)")
     ap.add_argument("--train-batch", type=int, default=128, help="instances the learned correction trains on")

@@ -60,7 +60,8 @@ struct psl1_problem {
     double *d_Ua = nullptr, *d_Ub = nullptr, *d_Us = nullptr, *d_Fv = nullptr, *d_Gold = nullptr;
     double *d_incr = nullptr, *d_work = nullptr, *d_ring = nullptr, *d_corr = nullptr;
     int *d_nfirst = nullptr, *d_active = nullptr, *d_counter = nullptr;
-    int* d_gmode = nullptr;   // per instance: the stored G_old values are FP32-step values
+    int* d_gmode = nullptr;
+    int* d_order = nullptr;   // instance order of the coarse sweep (B) and of the serial solver (B)   // per instance: the stored G_old values are FP32-step values
     int2* d_units = nullptr;
     int nunits = 0;
     DevStatus* d_status = nullptr;
@@ -586,6 +587,22 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     });
     h->nunits = (int)units.size();
     CTRY(dalloc(h, &h->d_units, units.size()));
+    // One CTA (or cluster) per instance runs each sequential chain: the coarse sweep
+    // (P coarse steps, cost ~ K^3 or K (Qx + Qy) per step) and the serial solver (N fine
+    // steps).  Launched longest first, the longest chains start on SMs of their own;
+    // with more instances than SMs the shorter ones share.
+    std::vector<int> order(2 * (size_t)batch);
+    for (int b = 0; b < batch; ++b) order[b] = order[batch + b] = b;
+    auto step_cost = [](const InstDev& I) {
+        return I.dim == 2 ? (double)I.K * (I.Q + I.Qy) : (double)I.K * I.K * I.K;
+    };
+    std::stable_sort(order.begin(), order.begin() + batch, [&](int x, int y) {
+        return step_cost(h->inst[x]) > step_cost(h->inst[y]);
+    });
+    std::stable_sort(order.begin() + batch, order.end(), [&](int x, int y) {
+        return h->inst[x].N * step_cost(h->inst[x]) > h->inst[y].N * step_cost(h->inst[y]);
+    });
+    CTRY(dalloc(h, &h->d_order, order.size()));
     for (size_t t = 0; t < jobs.size(); ++t) {
         const TabDev& T = h->tabs[t];
         jobs[t].xh = h->d_tp + T.oX;
@@ -618,6 +635,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
                             h->stream), "copy tables"));
     CTRY(cu(cudaMemcpyAsync(h->d_units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice,
                             h->stream), "copy units"));
+    CTRY(cu(cudaMemcpyAsync(h->d_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice,
+                            h->stream), "copy instance order"));
     CTRY(cu(cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream), "status"));
     if (!cheb_pool.empty())
         CTRY(cu(cudaMemcpyAsync(h->d_cheb, cheb_pool.data(), sizeof(double) * cheb_pool.size(),
@@ -663,6 +682,8 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.incr = h->d_incr;
     a.loose_above = 0.0;
     a.gmode = h->d_gmode;
+    a.sweep_order = h->d_order;
+    a.serial_order = h->d_order + batch;
     a.cheb = h->d_cheb;
     a.fstage_minb = 2;
     a.split2d = 1;

@@ -730,7 +730,8 @@ k_coarse_sweep(PathArgs a, const double* u0, const double* Uold, double* Unew, c
     __shared__ double red[NT / 32];
     __shared__ double s_num, s_den;
     const int csize = (D2 && a.split2d > 1) ? a.split2d : 1;
-    const int ii = blockIdx.x / csize, tid = threadIdx.x;
+    // the longest chains first: the first CTAs to start get an SM each, the rest share
+    const int ii = a.sweep_order ? a.sweep_order[blockIdx.x / csize] : blockIdx.x / csize, tid = threadIdx.x;
     if (csize > 1) {
         cv.sp.size = csize;
         cv.sp.rank = (int)cooperative_groups::this_cluster().block_rank();
@@ -839,7 +840,7 @@ k_serial_hyb(PathArgs a, const double* u0, double* Us)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Carve cv = carve<D2>(a, smem_raw);
-    const int ii = blockIdx.x;
+    const int ii = a.serial_order ? a.serial_order[blockIdx.x] : blockIdx.x;   // the longest chains first
     const InstDev& I = a.inst[ii];
     double* U = Us + I.oU;
     double* ring = a.ring + (size_t)blockIdx.x * a.ring_stride;

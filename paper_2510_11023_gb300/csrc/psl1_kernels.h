@@ -83,6 +83,8 @@ struct PathArgs {
     const df* bccd;          // the same as double-float
     int* gmode;              // per instance: 1 if the stored G_old values are FP32-step values
     double* corr;            // per-CTA-slot parareal corrections F_old(n) - G_old(n) of the sweep (Kmax)
+    const int* sweep_order;  // instance of each coarse-sweep CTA (cluster), longest chain first; may be null
+    const int* serial_order; // instance of each serial-solver CTA, longest chain first; may be null
     int split2d;             // 2D: CTAs of the cluster that shares each coarse-sweep step (1: none)
     Layout2D L2s;            // 2D: the layout of one CTA of such a cluster
 };
