@@ -38,6 +38,7 @@ UNIT = "fine_steps*modes/s"
 TARGET = 1e-8
 FIXED_TOL = TARGET             # increment tolerance of the stopping rule, fixed in advance
 INEXACT_ABOVE = (1e-4, 1e-5, 3e-6)   # increments above which early iterations take the FP32 step (candidates)
+REFINE_FACTORS = (1e-3, 1e-2, 1e-1)  # refined F steps of slices n > k stop at factor * e_{k-1} (candidates)
 
 
 def parse():
@@ -669,6 +670,17 @@ def main():
     ok = [k for k in cands if cands[k]["rel_err"] <= TARGET] or list(cands)
     best = cands[min(ok, key=lambda k: cands[k]["ms"])]
     coarse, inexact = best["coarse"], best["inexact_above"]
+    # then looser refined steps while the increment is large (MIXED 1D, with inexact iterations)
+    refine = 0.0
+    if inexact > 0.0 and not dim2:
+        for fac in REFINE_FACTORS:
+            pr.set_inexact_refinement(fac)
+            c = trial(coarse, inexact)
+            c["refine_factor"] = fac
+            cands[f"{coarse}|{inexact:g}|refine={fac:g}"] = c
+            if c["rel_err"] <= TARGET and c["ms"] < best["ms"]:
+                best, refine = c, fac
+        pr.set_inexact_refinement(refine)
     configure(coarse, inexact)
 
     # context only: the loosest increment tolerance that still reaches the target error,
@@ -785,7 +797,7 @@ def main():
         achieved = alg / max(fine_launches, 1) / (fine_avg_ms * 1e-3) / 1e12
         count = ("4QK + 2Q(2K+1) + K^3/3 + 2K^2 per fine step (transforms, Toeplitz+Hankel moments, "
                  "direct-solve count) x the fine steps of each launch")
-    traffic_key = f"{args.workload}|B={wl.B}|{args.precision}|{coarse}|inexact={inexact:g}"
+    traffic_key = f"{args.workload}|B={wl.B}|{args.precision}|{coarse}|inexact={inexact:g}|refine={refine:g}"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "frac_impl": achieved_impl / peak, "traffic": captured_traffic(traffic_key),
             "traffic_config": traffic_key, "kernel": "k_fstage",
@@ -819,7 +831,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "rel_err_vs_serial_fp64": err, "stop_tol": tol, "iterations": iters_all,
             "tuned_tolerance": tuned, "autotune": tune_info,
-            "coarse_propagator": coarse, "inexact_early_iterations": {"above": inexact},
+            "coarse_propagator": coarse, "inexact_early_iterations": {"above": inexact, "refine_factor": refine},
             "sweep_split_ctas": pr.sweep_split(),
             "configurations_tried": cands, "learned_training": train_info,
             "serial_fp64_ms": serial_fp64_ms, "serial_ms": serial_ms, "serial_uniform": uniform,

@@ -241,6 +241,20 @@ psl1_status psl1_set_graph(psl1_h h, int on);
  * same F and G throughout).                                                 */
 psl1_status psl1_set_inexact_fine(psl1_h h, double above);
 
+/* Looser refined F steps while the increment is large (off by default,
+ * factor = 0; no counterpart in the paper -- an inexact-solve choice like
+ * psl1_set_inexact_fine).  With factor > 0, from iteration k >= 1 on, the
+ * refined steps of slices n > k (those not taking the FP32 step) stop their
+ * iterative refinement once the measured or predicted correction is below
+ * min(1e-6, factor e_{k-1}) of the iterate, instead of the full target
+ * (1e-11 measured, 1e-13 predicted).  Slice n = k keeps the full target,
+ * so U^{k+1}_{0:k+1} stays exact, and the target tightens with e_k, so the
+ * iteration still ends at S_hyb.  F is computed afresh in every iteration,
+ * so no stored value has to be recomputed when the target changes.  MIXED
+ * 1D instances; a no-op otherwise.  Rebuilds the parareal graph.
+ * PSL1_ERR_ARG for negative or non-finite values.                          */
+psl1_status psl1_set_inexact_refinement(psl1_h h, double factor);
+
 /* Coarse propagator with c L1 substeps per slice (1 <= c <= the smallest m
  * of the batch; 1, the default, is the paper's one-step G of Eq.
  * CoarsePropagator).  G^(c)_n(U_{0:n}) is the fine propagator of Eq.

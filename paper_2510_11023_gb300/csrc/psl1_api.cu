@@ -681,6 +681,7 @@ psl1_status psl1_create(psl1_h* out, int batch, const psl1_instance* in, int P, 
     a.L2 = lay2;
     a.incr = h->d_incr;
     a.loose_above = 0.0;
+    a.refine_factor = 0.0;
     a.gmode = h->d_gmode;
     a.sweep_order = h->d_order;
     a.serial_order = h->d_order + batch;
@@ -1875,6 +1876,7 @@ psl1_status psl1_mlp_dataset(psl1_mlp_h mh, psl1_h data, int source, int iters)
     MCU(mh, cudaMemsetAsync(data->d_status, 0, sizeof(DevStatus), mh->stream));
     PathArgs run = data->pa;          // the data problem's own coarse propagator
     run.loose_above = 0.0;            // samples from refined F and G only
+    run.refine_factor = 0.0;
     PathArgs feat = data->pa;         // feature / sample layout of this network
     feat.mlp = mh->dev();
     std::vector<int> valid;
@@ -1973,6 +1975,18 @@ psl1_status psl1_mlp_train(psl1_mlp_h mh, psl1_h data, int epochs, int batch, fl
     }
     MCU(mh, cudaStreamSynchronize(mh->stream));
     return check_tc(mh);
+}
+
+psl1_status psl1_set_inexact_refinement(psl1_h h, double factor)
+{
+    if (!h) return fail(h, PSL1_ERR_ARG, "NULL handle");
+    if (!(factor >= 0.0) || !std::isfinite(factor)) return fail(h, PSL1_ERR_ARG, "factor must be finite and >= 0");
+    h->pa.refine_factor = factor;
+    if (h->par_graph) {   // the graph holds the kernels' arguments
+        cudaGraphExecDestroy(h->par_graph);
+        h->par_graph = nullptr;
+    }
+    return PSL1_OK;
 }
 
 psl1_status psl1_set_sweep_split(psl1_h h, int ctas)

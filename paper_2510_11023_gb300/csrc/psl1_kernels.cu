@@ -250,7 +250,7 @@ enum { WHERE_FINE = 1, WHERE_COARSE = 2, WHERE_UNI = 3, WHERE_ONE = 4 };
 template <bool D2>
 __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, const double* c,
                                        const double* hist, double te, double mu, double* out, Carve& cv,
-                                       bool one_solve = false)
+                                       bool one_solve = false, float ftol = 0.f)
 {
     const TabDev& Tb = a.tab[I.tab];
     int bad;
@@ -288,7 +288,8 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
             BPack<double, TILE> A{a.work + (size_t)blockIdx.x * a.work_stride};
             bad = step_fp64(I, Tb, a.tp, c, hist, te, mu, out, cv.F, A, cv.s);
         } else {
-            bad = step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, cv.s, cv.ms, cv.cg, a.prec == 2, one_solve);
+            bad = step_mixed(I, Tb, a.tp, c, hist, te, mu, out, cv.F, cv.s, cv.ms, cv.cg, a.prec == 2, one_solve,
+                             ftol);
         }
         // algorithmic FLOPs of the step: transforms (u, moments, load: 4 K^2 multiply-adds with
         // Q = 2K nodes), coefficient evaluation (~30 per node), and the solve -- FP64: Cholesky
@@ -344,9 +345,11 @@ constexpr int HC_R = 8;
 
 // dud_ready: the caller has already stored the coarse differences of rows
 // 0..n-1 in the CTA's slot (a sweep appends one row per step).
+// ftol: the refined 1D step's looser refinement target (0: the full one).
 template <bool D2>
 __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, double* Vout, double* out,
-                           Carve& cv, double* ring, bool one_solve, const SliceGrid& g, bool dud_ready = false)
+                           Carve& cv, double* ring, bool one_solve, const SliceGrid& g, bool dud_ready = false,
+                           float ftol = 0.f)
 {
     const InstDev& I = a.inst[ii];
     const int K = I.K, m = g.m, tid = threadIdx.x;
@@ -432,7 +435,7 @@ __device__ void fine_slice(const PathArgs& a, int ii, int n, const double* U, do
         }
         if (tid == 0 && a.flops && cv.sp.rank == 0) atomicAdd(a.flops + a.flop_slot, 2.0 * K * (r - 1 + n));
         __syncthreads();
-        int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n + g.dt * (r - 1), g.mu, cv.nxt, cv, one_solve);
+        int bad = do_step<D2>(a, I, cv.cur, cv.hist, I.dT * n + g.dt * (r - 1), g.mu, cv.nxt, cv, one_solve, ftol);
         if (bad >= 0 && threadIdx.x == 0) report(a.status, -2, ii, WHERE_FINE, n * m + r);
         check_finite(a, cv.nxt, K, ii, WHERE_FINE, n * m + r);
         for (int k = tid; k < K; k += NT) {
@@ -664,8 +667,17 @@ k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nuni
         // take the FP32 step.  Slice n = nfirst starts from exact states and stays
         // exact, so U^{k+1}_{k+1} and the fixed point are unchanged.
         const bool one_solve = n > nfirst[ii] && inexact_iteration(a, ii, nfirst[ii]);
+        // Looser refined steps (opt-in, MIXED 1D): after the first iteration the refined
+        // F of slices n > nfirst stops refining at refine_factor e_{k-1} of the iterate
+        // (at most 1e-6, at least the full target).  F is evaluated afresh in every
+        // iteration, so the iteration needs no consistency between them; slice nfirst
+        // keeps the full target and with it the exact prefix, and as e_k falls the
+        // target returns to the full one, so the fixed point is S_hyb.
+        float ftol = 0.f;
+        if (!one_solve && !D2 && a.prec == 1 && a.refine_factor > 0.0 && nfirst[ii] > 0 && n > nfirst[ii])
+            ftol = (float)fmin(1e-6, a.refine_factor * a.incr[ii]);
         fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring, one_solve,
-                       fine_grid(a, I));
+                       fine_grid(a, I), false, ftol);
     }
 }
 

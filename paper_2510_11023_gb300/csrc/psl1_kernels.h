@@ -77,6 +77,7 @@ struct PathArgs {
     Layout2D L2;
     const double* incr;      // last parareal increment e_k per instance (written by the correction sweep)
     double loose_above;      // > 0: inexact F stage while e_k > loose_above (MIXED only; 0: off)
+    double refine_factor;    // > 0: refined F steps of slices n > k stop refining at refine_factor e_{k-1}
     const double* cheb;      // collocation pool (nodes, sines, derivative matrices), may be null
     int fstage_minb;         // 1D F stage: CTAs per SM its registers are bounded for (2, 3 or 4)
     const double* bcc;       // coarse-substep weights mc^-a b(d + r/mc) (FP64), may be null

@@ -550,9 +550,12 @@ __device__ void residual_df(const InstDev& I, double mu, MixSmem& ms)
 // The step: c (K, shared) -> out (K, shared).  Returns the first bad pivot or -1.
 // one_solve: run the FP32 step (FP32 transforms, D and f, one FP32 solve, no
 // refinement) -- the inexact fine steps of early parareal iterations.
+// ftol > 0: the refinement may stop once the (measured or predicted) correction
+// is below ftol of the iterate instead of REFINE_TOL / REFINE_EST (a looser
+// refined step while parareal's increment is still large).
 __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, const double* c,
                           const double* hist, double te, double mu, double* out, double* F, StepSmem& s,
-                          MixSmem& ms, PcgSmem& cg, bool fp32_only, bool one_solve = false)
+                          MixSmem& ms, PcgSmem& cg, bool fp32_only, bool one_solve = false, float ftol = 0.f)
 {
     const int tid = threadIdx.x;
     fp32_only = fp32_only || one_solve;   // the inexact step is the FP32 step
@@ -581,8 +584,9 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
         zmax = block_max(zmax, ms.red);
         __syncthreads();
         xmax = block_max(xmax, ms.red);
-        const bool small = zmax <= REFINE_TOL * xmax;
-        const bool predicted = sweep >= 1 && zmax < zprev && zmax * zmax <= REFINE_EST * xmax * zprev;
+        const bool small = zmax <= fmaxf(REFINE_TOL, ftol) * xmax;
+        const bool predicted =
+            sweep >= 1 && zmax < zprev && zmax * zmax <= fmaxf(REFINE_EST, ftol) * xmax * zprev;
         if (fp32_only || small || predicted || sweep >= 6 || *s.bad >= 0) break;
         zprev = zmax;
         if (tid == 0) ms.flag[2] += 1;

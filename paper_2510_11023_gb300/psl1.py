@@ -72,6 +72,7 @@ SIGNATURES = {
     "psl1_keep_iterates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "psl1_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "psl1_set_inexact_fine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "psl1_set_inexact_refinement": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "psl1_set_coarse_substeps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "psl1_set_sweep_split": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "psl1_get_sweep_split": (ctypes.c_int, [ctypes.c_void_p, _I]),
@@ -299,6 +300,10 @@ class Problem:
         """Inexact early iterations: the FP32 step on slices n > k while the last
         increment exceeds `above` (0: off).  MIXED handles (1D and 2D)."""
         _chk(self.L.psl1_set_inexact_fine(self.h, float(above)), self.h)
+
+    def set_inexact_refinement(self, factor: float):
+        """Refined F steps of slices n > k stop refining at factor * e_{k-1} (0: off). MIXED 1D."""
+        _chk(self.L.psl1_set_inexact_refinement(self.h, float(factor)), self.h)
 
     def get_iterate(self, k: int) -> list:
         out = np.zeros(int(self.offU[-1]))

@@ -156,3 +156,49 @@ def test_serial_coarse_solution_ignores_the_inexact_setting():
         pr.solve_serial("coarse")
         C1 = pr.get_coeffs("serial", flat=True)
     assert np.array_equal(C0, C1)
+
+
+def test_looser_refinement_keeps_exact_prefix_and_fixed_point():
+    # psl1_set_inexact_refinement: refined steps of slices n > k stop at factor * e_{k-1}.
+    # Slice n = k keeps the full target, so U^{k}_{0:k} = S_hyb to 1e-13 after k
+    # iterations, and the iteration still ends at S_hyb.
+    wl = _batch()
+    with psl1.Problem(wl, precision="mixed") as pr:
+        pr.solve_serial("hybrid")
+        S = pr.get_coeffs("serial")
+        pr.solve_parareal(tol=1e-12)
+        f_full = pr.stats()["flop_fine"]
+        k_full = pr.get_iterations().max()
+        pr.set_inexact_refinement(1e-2)
+        pr.keep_iterates(True)
+        k = pr.solve_parareal(tol=1e-12)
+        f_loose = pr.stats()["flop_fine"]
+        for j in range(k + 1):
+            Uj = pr.get_iterate(j)
+            for b in range(wl.B):
+                top = min(j, wl.P)
+                assert np.abs(Uj[b][: top + 1] - S[b][: top + 1]).max() <= 1e-13 * np.abs(S[b]).max(), (j, b)
+        U = pr.get_coeffs("parareal")
+    for b in range(wl.B):
+        assert rel(U[b], S[b]) < TOL_SOLVE, b
+    assert k <= k_full + 1
+    if k == k_full:
+        assert f_loose < f_full, (f_full, f_loose)
+
+
+def test_looser_refinement_graph_equals_host_and_rejects_bad_values():
+    wl = _batch()
+    out = []
+    for graph in (False, True):
+        with psl1.Problem(wl, precision="mixed") as pr:
+            pr.set_inexact_fine(1e-4)
+            pr.set_inexact_refinement(1e-3)
+            pr.set_graph(graph)
+            pr.solve_parareal(tol=1e-11, allow_not_converged=True)
+            out.append((pr.get_coeffs("parareal", flat=True), pr.get_iterations()))
+            for bad in (-1.0, float("nan"), float("inf")):
+                with pytest.raises(psl1.PSL1Error) as ei:
+                    pr.set_inexact_refinement(bad)
+                assert ei.value.status == -1
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][0], out[1][0])
