@@ -670,9 +670,9 @@ def main():
     ok = [k for k in cands if cands[k]["rel_err"] <= TARGET] or list(cands)
     best = cands[min(ok, key=lambda k: cands[k]["ms"])]
     coarse, inexact = best["coarse"], best["inexact_above"]
-    # then looser refined steps while the increment is large (MIXED 1D, with inexact iterations)
+    # then looser refined steps while the increment is large (MIXED, with inexact iterations)
     refine = 0.0
-    if inexact > 0.0 and not dim2:
+    if inexact > 0.0:
         for fac in REFINE_FACTORS:
             pr.set_inexact_refinement(fac)
             c = trial(coarse, inexact)

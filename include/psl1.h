@@ -251,7 +251,7 @@ psl1_status psl1_set_inexact_fine(psl1_h h, double above);
  * so U^{k+1}_{0:k+1} stays exact, and the target tightens with e_k, so the
  * iteration still ends at S_hyb.  F is computed afresh in every iteration,
  * so no stored value has to be recomputed when the target changes.  MIXED
- * 1D instances; a no-op otherwise.  Rebuilds the parareal graph.
+ * instances (1D and 2D); a no-op otherwise.  Rebuilds the parareal graph.
  * PSL1_ERR_ARG for negative or non-finite values.                          */
 psl1_status psl1_set_inexact_refinement(psl1_h h, double factor);
 

@@ -264,7 +264,7 @@ __device__ __forceinline__ int do_step(const PathArgs& a, const InstDev& I, cons
             bad = step2d_fp64(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad, cv.sp);
         else
             bad = step2d_mixed(I, Tb, TY, a.tp, c, hist, te, mu, out, cv.F, cv.s2, cv.s.bad, a.prec == 2 || one_solve,
-                               cv.sp);
+                               cv.sp, ftol);
         // algorithmic FLOPs: each operator application is four folded one-axis
         // transforms, 4 (Mx My Qy/2 + Mx Qy Qx/2) multiply-adds; the set-up
         // (node values, load, diagonal) costs one application, the coefficient
@@ -667,14 +667,14 @@ k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nuni
         // take the FP32 step.  Slice n = nfirst starts from exact states and stays
         // exact, so U^{k+1}_{k+1} and the fixed point are unchanged.
         const bool one_solve = n > nfirst[ii] && inexact_iteration(a, ii, nfirst[ii]);
-        // Looser refined steps (opt-in, MIXED 1D): after the first iteration the refined
+        // Looser refined steps (opt-in, MIXED): after the first iteration the refined
         // F of slices n > nfirst stops refining at refine_factor e_{k-1} of the iterate
         // (at most 1e-6, at least the full target).  F is evaluated afresh in every
         // iteration, so the iteration needs no consistency between them; slice nfirst
         // keeps the full target and with it the exact prefix, and as e_k falls the
         // target returns to the full one, so the fixed point is S_hyb.
         float ftol = 0.f;
-        if (!one_solve && !D2 && a.prec == 1 && a.refine_factor > 0.0 && nfirst[ii] > 0 && n > nfirst[ii])
+        if (!one_solve && a.prec == 1 && a.refine_factor > 0.0 && nfirst[ii] > 0 && n > nfirst[ii])
             ftol = (float)fmin(1e-6, a.refine_factor * a.incr[ii]);
         fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring, one_solve,
                        fine_grid(a, I), false, ftol);

@@ -639,10 +639,12 @@ __device__ int step2d_fp64(const InstDev& I, const TabDev& TX, const TabDev& TY,
     return flag[0];
 }
 
-// Mixed path (fp32_only: FP32 coefficients and a single FP32 solve).
+// Mixed path (fp32_only: FP32 coefficients and a single FP32 solve; ftol > 0:
+// the refinement may stop at that fraction of the iterate, as in the 1D step).
 __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY, const double* tp,
                             const double* c, const double* hist, double te, double mu, double* out, double* F,
-                            const Step2D& S, int* flag, bool fp32_only, const Split& sp = Split{})
+                            const Step2D& S, int* flag, bool fp32_only, const Split& sp = Split{},
+                            float ftol = 0.f)
 {
     const Dims2 g = dims2(I, sp);
     const int tid = threadIdx.x, QQ = g.Qx * g.Qyl, K = g.K;
@@ -715,8 +717,9 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
         zmax = block_maxT(zmax, red);
         xmax = block_maxT(xmax, red);
         // stop on a small correction, or when the observed contraction predicts one (as in 1D)
-        const bool small = zmax <= REFINE_TOL * xmax;
-        const bool predicted = sweep >= 1 && zmax < zprev && zmax * zmax <= REFINE_EST * xmax * zprev;
+        const bool small = zmax <= fmaxf(REFINE_TOL, ftol) * xmax;
+        const bool predicted =
+            sweep >= 1 && zmax < zprev && zmax * zmax <= fmaxf(REFINE_EST, ftol) * xmax * zprev;
         if (fp32_only || small || predicted || sweep >= 6 || flag[0] >= 0) break;
         zprev = zmax;
         if (tid == 0) flag[2] += 1;

@@ -302,7 +302,7 @@ class Problem:
         _chk(self.L.psl1_set_inexact_fine(self.h, float(above)), self.h)
 
     def set_inexact_refinement(self, factor: float):
-        """Refined F steps of slices n > k stop refining at factor * e_{k-1} (0: off). MIXED 1D."""
+        """Refined F steps of slices n > k stop refining at factor * e_{k-1} (0: off). MIXED 1D and 2D."""
         _chk(self.L.psl1_set_inexact_refinement(self.h, float(factor)), self.h)
 
     def get_iterate(self, k: int) -> list:

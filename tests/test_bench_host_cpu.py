@@ -73,3 +73,25 @@ def test_reference_arm_context_timings_of_the_small_configurations():
     for r in out.values():
         assert r["serial_uniform_s"] > 0 and r["serial_hybrid_s"] > 0 and r["parareal_iterations"] >= 1
         assert any(k.startswith("parareal_s_threads") for k in r)
+
+
+def test_roofline_traffic_only_from_a_matching_capture(tmp_path, monkeypatch):
+    # the DRAM traffic of a committed ncu capture is reported only while the CUDA
+    # sources (their digest) and the benched configuration are the captured ones
+    key = "batched1d|B=256|mixed|l1x2|inexact=3e-06|refine=0.01"
+    f = tmp_path / "capture.md"
+
+    def write(digest, config, nbytes="123456789"):
+        f.write_text(f"# capture\n\n- `sources_sha256`: `{digest}`\n- `config`: `{config}`\n"
+                     f"- `bytes_per_launch`: `{nbytes}`\n- other: text\n")
+
+    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(f))
+    assert bench.captured_traffic(key) is None                      # no file
+    write(bench.source_digest(), key)
+    assert bench.captured_traffic(key) == 123456789.0
+    assert bench.captured_traffic(key.replace("l1x2", "l1x4")) is None
+    write("0" * 64, key)
+    assert bench.captured_traffic(key) is None
+    write(bench.source_digest(), key, "not-a-number")
+    assert bench.captured_traffic(key) is None
+    assert len(bench.source_digest()) == 64

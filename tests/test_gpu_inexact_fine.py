@@ -202,3 +202,21 @@ def test_looser_refinement_graph_equals_host_and_rejects_bad_values():
                 assert ei.value.status == -1
     assert np.array_equal(out[0][1], out[1][1])
     assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_looser_refinement_2d_exact_prefix_and_fixed_point():
+    wl = workloads.small_batch_2d()
+    with psl1.Problem(wl, precision="mixed") as pr:
+        pr.solve_serial("hybrid")
+        S = pr.get_coeffs("serial")
+        pr.set_inexact_fine(1e-4)
+        pr.set_inexact_refinement(1e-2)
+        pr.keep_iterates(True)
+        k = pr.solve_parareal(tol=1e-12)
+        for j in range(k + 1):
+            Uj = pr.get_iterate(j)
+            for b in range(wl.B):
+                assert np.abs(Uj[b][: j + 1] - S[b][: j + 1]).max() <= 1e-13 * np.abs(S[b]).max(), (j, b)
+        U = pr.get_coeffs("parareal")
+    for b in range(wl.B):
+        assert rel(U[b], S[b]) < TOL_SOLVE, b
