@@ -78,7 +78,7 @@ def test_reference_arm_context_timings_of_the_small_configurations():
 def test_roofline_traffic_only_from_a_matching_capture(tmp_path, monkeypatch):
     # the DRAM traffic of a committed ncu capture is reported only while the CUDA
     # sources (their digest) and the benched configuration are the captured ones
-    key = "batched1d|B=256|mixed|l1x2|inexact=3e-06|refine=0.01"
+    key = "batched1d|B=256|mixed|l1x2|inexact=3e-06"
     f = tmp_path / "capture.md"
 
     def write(digest, config, nbytes="123456789"):
