@@ -247,7 +247,10 @@ psl1_status psl1_set_inexact_fine(psl1_h h, double above);
  * refined steps of slices n > k (those not taking the FP32 step) stop their
  * iterative refinement once the measured or predicted correction is below
  * min(1e-6, factor e_{k-1}) of the iterate, instead of the full target
- * (1e-11 measured, 1e-13 predicted).  Slice n = k keeps the full target,
+ * (1e-11 measured, 1e-13 predicted); those taking the FP32 step solve to
+ * a relative residual of min(1e-4, factor e_{k-1}) instead of 1e-7 (the
+ * coarse propagator's FP32 steps are unchanged, since G must be the same
+ * function at both call sites).  Slice n = k keeps the full target,
  * so U^{k+1}_{0:k+1} stays exact, and the target tightens with e_k, so the
  * iteration still ends at S_hyb.  F is computed afresh in every iteration,
  * so no stored value has to be recomputed when the target changes.  MIXED

@@ -673,9 +673,11 @@ k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nuni
         // iteration, so the iteration needs no consistency between them; slice nfirst
         // keeps the full target and with it the exact prefix, and as e_k falls the
         // target returns to the full one, so the fixed point is S_hyb.
+        // The FP32 steps of those slices likewise solve to a relative residual of
+        // factor e_{k-1} (at most 1e-4, at least the FP32 step's own 1e-7).
         float ftol = 0.f;
-        if (!one_solve && a.prec == 1 && a.refine_factor > 0.0 && nfirst[ii] > 0 && n > nfirst[ii])
-            ftol = (float)fmin(1e-6, a.refine_factor * a.incr[ii]);
+        if (a.prec == 1 && a.refine_factor > 0.0 && nfirst[ii] > 0 && n > nfirst[ii])
+            ftol = (float)fmin(one_solve ? 1e-4 : 1e-6, a.refine_factor * a.incr[ii]);
         fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring, one_solve,
                        fine_grid(a, I), false, ftol);
     }

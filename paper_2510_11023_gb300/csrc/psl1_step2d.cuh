@@ -703,7 +703,7 @@ __device__ int step2d_mixed(const InstDev& I, const TabDev& TX, const TabDev& TY
         S.z[k] = (float)rk;
     }
     __syncthreads();
-    const float rtol = fp32_only ? PCG2_RTOL32 : I.inner_rtol;   // tunable in the refined step
+    const float rtol = fp32_only ? fmaxf(PCG2_RTOL32, ftol) : I.inner_rtol;   // tunable in the refined step
     pcg2d<NumF, 2, 4, 4>(g, tf, (float)mu, S.wd32, S.z, S, flag, PCG2_MAXIT32, rtol, sp);
     float zprev = 0.f;
     for (int sweep = 0;; ++sweep) {

@@ -552,7 +552,8 @@ __device__ void residual_df(const InstDev& I, double mu, MixSmem& ms)
 // refinement) -- the inexact fine steps of early parareal iterations.
 // ftol > 0: the refinement may stop once the (measured or predicted) correction
 // is below ftol of the iterate instead of REFINE_TOL / REFINE_EST (a looser
-// refined step while parareal's increment is still large).
+// refined step while parareal's increment is still large); the FP32 step solves
+// to a relative residual of max(PCG_RTOL, ftol).
 __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, const double* c,
                           const double* hist, double te, double mu, double* out, double* F, StepSmem& s,
                           MixSmem& ms, PcgSmem& cg, bool fp32_only, bool one_solve = false, float ftol = 0.f)
@@ -570,7 +571,7 @@ __device__ int step_mixed(const InstDev& I, const TabDev& Tb, const double* tp, 
     if (tid == 0) *s.bad = -1;
     __syncthreads();
     // inner tolerance: the FP32 step's own; the refined step's is tunable per instance
-    const float rtol = fp32_only ? PCG_RTOL : I.inner_rtol;
+    const float rtol = fp32_only ? fmaxf(PCG_RTOL, ftol) : I.inner_rtol;
     pcg32(I, mu, ms, cg, PCG_MAXIT, rtol);
     float zprev = 0.f;
     for (int sweep = 0;; ++sweep) {
