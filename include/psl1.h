@@ -243,8 +243,8 @@ psl1_status psl1_set_inexact_fine(psl1_h h, double above);
 
 /* Looser refined F steps while the increment is large (off by default,
  * factor = 0; no counterpart in the paper -- an inexact-solve choice like
- * psl1_set_inexact_fine).  With factor > 0, from iteration k >= 1 on, the
- * refined steps of slices n > k (those not taking the FP32 step) stop their
+ * psl1_set_inexact_fine).  With factor > 0, in iteration k (e_{-1} taken as
+ * 1), the refined steps of slices n > k (those not taking the FP32 step) stop their
  * iterative refinement once the measured or predicted correction is below
  * min(1e-6, factor e_{k-1}) of the iterate, instead of the full target
  * (1e-11 measured, 1e-13 predicted); those taking the FP32 step solve to

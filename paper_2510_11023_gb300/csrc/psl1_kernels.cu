@@ -667,17 +667,17 @@ k_fstage(PathArgs a, const double* Uold, double* Fv, const int2* units, int nuni
         // take the FP32 step.  Slice n = nfirst starts from exact states and stays
         // exact, so U^{k+1}_{k+1} and the fixed point are unchanged.
         const bool one_solve = n > nfirst[ii] && inexact_iteration(a, ii, nfirst[ii]);
-        // Looser refined steps (opt-in, MIXED): after the first iteration the refined
-        // F of slices n > nfirst stops refining at refine_factor e_{k-1} of the iterate
-        // (at most 1e-6, at least the full target).  F is evaluated afresh in every
+        // Looser refined steps (opt-in, MIXED): the refined F of slices n > nfirst stops
+        // refining at refine_factor e_{k-1} of the iterate (at most 1e-6, at least the
+        // full target; e_{-1} is taken as 1).  F is evaluated afresh in every
         // iteration, so the iteration needs no consistency between them; slice nfirst
         // keeps the full target and with it the exact prefix, and as e_k falls the
         // target returns to the full one, so the fixed point is S_hyb.
         // The FP32 steps of those slices likewise solve to a relative residual of
         // factor e_{k-1} (at most 1e-4, at least the FP32 step's own 1e-7).
         float ftol = 0.f;
-        if (a.prec == 1 && a.refine_factor > 0.0 && nfirst[ii] > 0 && n > nfirst[ii])
-            ftol = (float)fmin(one_solve ? 1e-4 : 1e-6, a.refine_factor * a.incr[ii]);
+        if (a.prec == 1 && a.refine_factor > 0.0 && n > nfirst[ii])
+            ftol = (float)fmin(one_solve ? 1e-4 : 1e-6, a.refine_factor * (nfirst[ii] > 0 ? a.incr[ii] : 1.0));
         fine_slice<D2>(a, ii, n, Uold + I.oU, nullptr, Fv + I.oPK + (size_t)n * I.K, cv, ring, one_solve,
                        fine_grid(a, I), false, ftol);
     }

@@ -159,7 +159,8 @@ def test_serial_coarse_solution_ignores_the_inexact_setting():
 
 
 def test_looser_refinement_keeps_exact_prefix_and_fixed_point():
-    # psl1_set_inexact_refinement: refined steps of slices n > k stop at factor * e_{k-1}.
+    # psl1_set_inexact_refinement: refined steps of slices n > k stop at factor * e_{k-1}
+    # (e_{-1} = 1).
     # Slice n = k keeps the full target, so U^{k}_{0:k} = S_hyb to 1e-13 after k
     # iterations, and the iteration still ends at S_hyb.
     wl = _batch()
