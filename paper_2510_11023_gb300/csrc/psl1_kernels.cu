@@ -202,7 +202,7 @@ Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long
     const long long e = f64 ? 8 : 4;   // CG vector element
     long long bytes[R2_COUNT];
     bytes[R2_BAD] = 16;
-    bytes[R2_RED] = 8 * 2 * (NT / 32);
+    bytes[R2_RED] = 8 * 4 * (NT / 32);   // two buffers of two sums (8-byte elements)
     bytes[R2_SPLIT] = split > 1 ? 16 + 8LL * 2 * Kmax : 0;   // all-reduction counter + two partial buffers
     bytes[R2_DINV] = e * Kmax;
     bytes[R2_PX] = e * Kmax;

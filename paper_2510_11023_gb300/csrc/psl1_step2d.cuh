@@ -323,7 +323,7 @@ struct Step2D {
     double *xr, *rhs;             // K: refinement iterate, right-hand side (mixed)
     float* z;                     // K: FP32 correction (mixed)
     float* tab32;                 // FP32 tables Sx, Dx, Sy, Dy (M x Qh each)
-    void* red;                    // reduction scratch (2 NT/32 doubles)
+    void* red;                    // reduction scratch (4 NT/32 doubles)
 };
 
 // A v -> out (K): the four folded one-axis transforms.
@@ -459,24 +459,30 @@ __device__ __forceinline__ Node2df node2_df(const InstDev& I, const TabDev& TX, 
 }
 
 // ------------------------------------------------------------------ block reductions
+// Block sums of a and b (every thread gets them, the same order of addition)
+// with one barrier: consecutive calls use the two halves of red
+// in turn (buf toggles), so a call never overwrites the half that threads may
+// still read from the call before; the barrier of the call in between orders
+// them.  red holds 2 x (2 NT/32) elements.
 template <typename T>
-__device__ __forceinline__ void block_sum2T(T& a, T& b, T* red)
+__device__ __forceinline__ void block_sum2T_db(T& a, T& b, T* red, int& buf)
 {
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
     }
-    __syncthreads();
+    T* r = red + buf * (2 * (NT / 32));
+    buf ^= 1;
     if ((threadIdx.x & 31) == 0) {
-        red[threadIdx.x >> 5] = a;
-        red[NT / 32 + (threadIdx.x >> 5)] = b;
+        r[threadIdx.x >> 5] = a;
+        r[NT / 32 + (threadIdx.x >> 5)] = b;
     }
     __syncthreads();
     T sa = 0, sb = 0;
 #pragma unroll
     for (int w = 0; w < NT / 32; ++w) {
-        sa += red[w];
-        sb += red[NT / 32 + w];
+        sa += r[w];
+        sb += r[NT / 32 + w];
     }
     a = sa;
     b = sb;
@@ -540,7 +546,10 @@ __device__ void pcg2d(const Dims2& g, const Tabs2<Nm>& tb, typename Nm::V mu, co
         rz += rk * zk;
         rr += rk * rk;
     }
-    block_sum2T(rz, rr, red);
+    // the sums below alternate between the two halves of red (block_maxT's last
+    // barrier orders the first one after its reads)
+    int buf = 0;
+    block_sum2T_db(rz, rr, red, buf);   // its barrier also publishes x, r and p
     const T stop = rtol * rtol * rr;
     for (int it = 0; it < maxit && rr > T(0); ++it) {
         if (tid == 0) flag[1] += 1;
@@ -551,7 +560,7 @@ __device__ void pcg2d(const Dims2& g, const Tabs2<Nm>& tb, typename Nm::V mu, co
             q[k] = qk;
             pq += p[k] * qk;
         }
-        block_sum2T(pq, zero, red);
+        block_sum2T_db(pq, zero, red, buf);
         if (!(pq > T(0))) {   // (I + mu A) not positive definite (D <= 0 somewhere)
             if (tid == 0 && flag[0] < 0) flag[0] = 0;
             break;
@@ -567,7 +576,7 @@ __device__ void pcg2d(const Dims2& g, const Tabs2<Nm>& tb, typename Nm::V mu, co
             rzn += rk * zk;
             rrn += rk * rk;
         }
-        block_sum2T(rzn, rrn, red);
+        block_sum2T_db(rzn, rrn, red, buf);
         if (rrn <= stop) break;
         const T be = rz > T(0) ? rzn / rz : T(0);
         rz = rzn;
