@@ -68,9 +68,8 @@ __device__ __forceinline__ Carve carve2d(const PathArgs& a, char* base)
     c.s2.tab32 = static_cast<float*>(at2(R2_TAB32));
     c.s2.red = at2(R2_RED);
     if (L.off[R2_SPLIT] >= 0) {   // rank and size are set by the kernel that splits the step
-        c.sp.nred = static_cast<int*>(at2(R2_SPLIT));
         c.sp.pb = reinterpret_cast<double*>(static_cast<char*>(at2(R2_SPLIT)) + 16);
-        c.sp.stride = a.Kmax;
+        c.sp.stride = a.Kmax + 8;   // >= K + size - 1 (size <= 8)
     }
     return c;
 }
@@ -203,7 +202,7 @@ Layout2D make_layout2d(int prec, int Kmax, long long nT, long long nN, long long
     long long bytes[R2_COUNT];
     bytes[R2_BAD] = 16;
     bytes[R2_RED] = 8 * 4 * (NT / 32);   // two buffers of two sums (8-byte elements)
-    bytes[R2_SPLIT] = split > 1 ? 16 + 8LL * 2 * Kmax : 0;   // all-reduction counter + two partial buffers
+    bytes[R2_SPLIT] = split > 1 ? 16 + 8LL * 2 * (Kmax + 8) : 0;   // receive and gather buffers
     bytes[R2_DINV] = e * Kmax;
     bytes[R2_PX] = e * Kmax;
     bytes[R2_PR] = e * Kmax;
@@ -749,9 +748,8 @@ k_coarse_sweep(PathArgs a, const double* u0, const double* Uold, double* Unew, c
     if (csize > 1) {
         cv.sp.size = csize;
         cv.sp.rank = (int)cooperative_groups::this_cluster().block_rank();
-        if (tid == 0) *cv.sp.nred = 0;
-        // every CTA of the cluster is running (and has set its counter) before any
-        // reads another's shared memory
+        // every CTA of the cluster is running before any writes into another's
+        // shared memory
         cooperative_groups::this_cluster().sync();
     }
     const InstDev& I = a.inst[ii];

@@ -246,9 +246,8 @@ __device__ void axis_bwd(int ncomp, bool sum, AxisOp<Nm> o0, AxisOp<Nm> o1, int 
 // the one-CTA step.
 struct Split {
     int rank = 0, size = 1;
-    double* pb = nullptr;   // this CTA's partial-sum buffers in shared memory: 2 x stride 8-byte slots
-    int stride = 0;
-    int* nred = nullptr;    // shared: all-reductions done (selects the buffer)
+    double* pb = nullptr;   // this CTA's receive and gather buffers in shared memory: 2 x stride 8-byte slots
+    int stride = 0;         // >= K + size - 1
 };
 
 struct Dims2 {
@@ -283,10 +282,15 @@ __device__ __forceinline__ int col_global(const Dims2& g, int jl)
 }
 
 // Sum of the CTAs' partial vectors v (K, this CTA's partial on entry, the
-// cluster's sum on return, the same in every CTA: each adds the partials in
-// rank order).  The buffers alternate between calls; a call writes the buffer
-// the call before the last one read, and the cluster barrier of the call in
-// between orders the two.
+// cluster's sum on return, the same in every CTA), as a reduce-scatter and an
+// all-gather that move data only by stores into other CTAs' shared memory:
+//   1. entry k of every partial goes to the receive buffer of the CTA that owns
+//      k (slices of S = ceil(K / size) entries), at the row of the sender;
+//   2. each CTA adds the rows of its slice in rank order and stores the sums
+//      into the gather buffer of every CTA;
+//   3. each CTA copies its gather buffer into v.
+// Two cluster barriers.  A buffer is written again only after the next call's
+// first barrier, which every CTA reaches after it has read this call's data.
 template <class Nm>
 __device__ void split_allreduce(const Split& sp, typename Nm::V* v, int K)
 {
@@ -294,15 +298,22 @@ __device__ void split_allreduce(const Split& sp, typename Nm::V* v, int K)
     using V = typename Nm::V;
     namespace cgx = cooperative_groups;
     cgx::cluster_group cl = cgx::this_cluster();
-    V* mine = reinterpret_cast<V*>(sp.pb + (size_t)(*sp.nred & 1) * sp.stride);
-    for (int k = threadIdx.x; k < K; k += NT) mine[k] = v[k];
-    cl.sync();
+    const int C = sp.size, S = (K + C - 1) / C;
+    V* recv = reinterpret_cast<V*>(sp.pb);               // C x S: row r = rank r's entries of my slice
+    V* gat = reinterpret_cast<V*>(sp.pb + sp.stride);    // K: the sums
     for (int k = threadIdx.x; k < K; k += NT) {
-        V acc = *cl.map_shared_rank(mine + k, 0);
-        for (int r = 1; r < sp.size; ++r) acc = Nm::add(acc, *cl.map_shared_rank(mine + k, r));
-        v[k] = acc;
+        const int owner = k / S;
+        *cl.map_shared_rank(recv + (size_t)sp.rank * S + (k - owner * S), owner) = v[k];
     }
-    if (threadIdx.x == 0) ++*sp.nred;   // every thread read the count above, before cl.sync()
+    cl.sync();
+    const int k0 = sp.rank * S;
+    for (int j = threadIdx.x; j < S && k0 + j < K; j += NT) {
+        V acc = recv[j];
+        for (int r = 1; r < C; ++r) acc = Nm::add(acc, recv[(size_t)r * S + j]);
+        for (int r = 0; r < C; ++r) *cl.map_shared_rank(gat + k0 + j, r) = acc;
+    }
+    cl.sync();
+    for (int k = threadIdx.x; k < K; k += NT) v[k] = gat[k];
     __syncthreads();
 }
 
